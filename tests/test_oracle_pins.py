@@ -1,0 +1,442 @@
+"""Pins for the CPU oracle: checks against things other than the oracle itself.
+
+* Philox4x32-10 against cuRAND's host-side Philox generator, run as a black
+  box through its public API (no GPU needed).
+* Tyche's MIX against ChaCha20 from the ``cryptography`` package (Tyche's MIX
+  is the ChaCha quarter-round, Neves & Araujo 2011).
+* Tyche's seeding constants against their closed forms floor(2^32/phi) and
+  floor(2^32/pi).
+* Word->value maps against exact edge values; Box-Muller against the polar
+  invariants r^2 = -2 ln u1 and angle = 2 pi u2.
+* Threefry4x32-20 and Squares: no outside implementation exists here
+  (parity unpinned for their round functions); they are held to invariants
+  (bijectivity through an inverse written here, avalanche, uniformity).
+"""
+import ctypes
+import ctypes.util
+import math
+import os
+import struct
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+M32 = 0xFFFFFFFF
+
+# ---------------------------------------------------------------- Philox ----
+
+CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161  # public enum value of curandRngType_t
+
+
+def _curand():
+    for cand in ("/usr/local/cuda/lib64/libcurand.so", ctypes.util.find_library("curand")):
+        if not cand:
+            continue
+        try:
+            return ctypes.CDLL(cand)
+        except OSError:
+            continue
+    return None
+
+
+def _curand_host_philox(seed, n, offset=0):
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not available")
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
+        out = np.zeros(n, np.uint32)
+        assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(n)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 42, 0x5EED, 0x123456789ABCDEF0, 2**64 - 1])
+def test_philox_matches_curand_host_generator(orc, seed):
+    # cuRAND's host Philox4_32_10 emits, for seed S, block i of Philox4x32-10
+    # with counter (0, 0, i, 0) and key (lo32(S), hi32(S)): found by searching
+    # that black box's output for blocks of the oracle.
+    n = 4 * 512
+    ref = _curand_host_philox(seed, n)
+    key = (seed & M32, seed >> 32)
+    for i in list(range(0, 64)) + list(range(64, n // 4, 37)):
+        assert orc.philox4x32_10((0, 0, i, 0), key) == [int(v) for v in ref[4 * i:4 * i + 4]], i
+
+
+def test_philox_matches_curand_far_offsets(orc):
+    # Past the first 2^16 blocks, cuRAND's host generator puts block b at
+    # counter (lo32(b >> 16), hi32(b >> 16), b mod 2^16, 0) (found the same
+    # way); this exercises counter words c0 and c1.
+    seed = 7
+    for blk in (2**20 + 3, 2**31 + 5, 2**32 - 1, 2**50 + 7, 2**52 + 2**33 + 9):
+        ref = _curand_host_philox(seed, 4, offset=4 * blk)
+        hi = blk >> 16
+        assert orc.philox4x32_10((hi & M32, hi >> 32, blk & 0xFFFF, 0), (seed, 0)) == [int(v) for v in ref]
+
+
+def test_philox_weyl_constants_closed_form():
+    # The key-bump constants are floor(2^32 / golden ratio) and
+    # floor((sqrt(3) - 1) * 2^32); the cuRAND match above already pins the
+    # oracle to them, this checks the closed forms quoted in its comment.
+    phi_c = (math.isqrt(5 << 64) - (1 << 32)) // 2          # floor(2^32 (sqrt5-1)/2)
+    sqrt3_c = math.isqrt(3 << 64) - (1 << 32)                # floor(2^32 (sqrt3-1))
+    assert phi_c == 0x9E3779B9
+    assert sqrt3_c == 0xBB67AE85
+
+
+# ----------------------------------------------------------------- Tyche ----
+
+def _chacha20_block_via_mix(orc, key_words, nonce_words):
+    """ChaCha20 block function with the quarter-round taken from the oracle."""
+    sigma = struct.unpack("<4I", b"expand 32-byte k")
+    init = list(sigma) + list(key_words) + list(nonce_words)
+    x = list(init)
+
+    def qr(a, b, c, d):
+        x[a], x[b], x[c], x[d] = orc.tyche_mix([x[a], x[b], x[c], x[d]])
+
+    for _ in range(10):
+        qr(0, 4, 8, 12); qr(1, 5, 9, 13); qr(2, 6, 10, 14); qr(3, 7, 11, 15)
+        qr(0, 5, 10, 15); qr(1, 6, 11, 12); qr(2, 7, 8, 13); qr(3, 4, 9, 14)
+    return struct.pack("<16I", *[(x[i] + init[i]) & M32 for i in range(16)])
+
+
+@pytest.mark.parametrize("trial", range(4))
+def test_tyche_mix_is_chacha_quarter_round(orc, trial):
+    from cryptography.hazmat.primitives.ciphers import Cipher, algorithms
+
+    rng = np.random.default_rng(100 + trial)
+    key = rng.integers(0, 256, 32, dtype=np.uint8).tobytes()
+    nonce = rng.integers(0, 256, 16, dtype=np.uint8).tobytes()
+    ref = Cipher(algorithms.ChaCha20(key, nonce), mode=None).encryptor().update(bytes(64))
+    got = _chacha20_block_via_mix(orc, struct.unpack("<8I", key), struct.unpack("<4I", nonce))
+    assert got == ref
+
+
+def test_tyche_seeding_constants_closed_form(orc):
+    import sympy
+
+    c_phi = (math.isqrt(5 << 64) - (1 << 32)) // 2           # floor(2^32 / phi)
+    c_pi = int(sympy.floor(sympy.Integer(2) ** 32 / sympy.pi))  # floor(2^32 / pi)
+    assert (c_phi, c_pi) == (2654435769, 1367130551)
+    for key64, ctr in [(0, 0), (0x0123456789ABCDEF, 5), (2**64 - 1, 2**32 - 1)]:
+        st = [key64 >> 32, key64 & M32, c_phi, c_pi ^ ctr]
+        for _ in range(20):
+            st = orc.tyche_mix(st)
+        assert orc.tyche_init(key64, ctr) == st
+
+
+def test_tyche_words_are_b_after_each_mix(orc):
+    st = orc.tyche_init(99, 3)
+    words = []
+    for _ in range(10):
+        st = orc.tyche_mix(st)
+        words.append(st[1])
+    assert list(orc.stream_words(orc.TYCHE, 99, 3, 0, 10)) == words
+
+
+# ---------------------------------------------------------------- Threefry --
+
+_TF_ROT = [(10, 26), (11, 21), (13, 27), (23, 5), (6, 20), (17, 11), (25, 10), (18, 20)]
+
+
+def _rotr(x, r):
+    return ((x >> r) | (x << (32 - r))) & M32
+
+
+def _threefry_inverse(out, key):
+    """Inverse of Threefry4x32-20 (undo each injection and round in reverse)."""
+    ks = list(key) + [0x1BD11BDA ^ key[0] ^ key[1] ^ key[2] ^ key[3]]
+    x = list(out)
+    for r in range(19, -1, -1):
+        if r % 4 == 3:
+            inj = (r + 1) // 4
+            x[3] = (x[3] - inj) & M32
+            for j in range(4):
+                x[j] = (x[j] - ks[(inj + j) % 5]) & M32
+        ra, rb = _TF_ROT[r % 8]
+        if r % 2 == 0:
+            x[3] = _rotr(x[3] ^ x[2], rb); x[2] = (x[2] - x[3]) & M32
+            x[1] = _rotr(x[1] ^ x[0], ra); x[0] = (x[0] - x[1]) & M32
+        else:
+            x[1] = _rotr(x[1] ^ x[2], rb); x[2] = (x[2] - x[1]) & M32
+            x[3] = _rotr(x[3] ^ x[0], ra); x[0] = (x[0] - x[3]) & M32
+    return [(x[j] - ks[j]) & M32 for j in range(4)]
+
+
+def test_threefry_is_a_bijection_of_the_counter(orc):
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        ctr = [int(v) for v in rng.integers(0, 2**32, 4, dtype=np.uint64)]
+        key = [int(v) for v in rng.integers(0, 2**32, 4, dtype=np.uint64)]
+        assert _threefry_inverse(orc.threefry4x32_20(ctr, key), key) == ctr
+
+
+# ------------------------------------------------------- all generators ----
+
+def _bits(a):
+    return np.unpackbits(np.asarray(a, np.uint32).view(np.uint8)).reshape(len(a), 32)
+
+
+@pytest.mark.parametrize("gen", [0, 1, 2, 3])
+def test_words_uniform_and_bit_balanced(orc, gen):
+    w = orc.fill(gen, orc.U32, seed=0x5EED, counter=0, n_streams=4096, dps=64)
+    n = w.size
+    # 256-bin chi-square on the top byte and per-bit balance, 5-sigma bounds.
+    hist = np.bincount(w >> 24, minlength=256)
+    chi2 = float(((hist - n / 256) ** 2 / (n / 256)).sum())
+    assert abs(chi2 - 255) < 5 * math.sqrt(2 * 255)
+    ones = _bits(w).sum(axis=0)
+    assert np.all(np.abs(ones - n / 2) < 5 * math.sqrt(n / 4))
+
+
+@pytest.mark.parametrize("gen", [0, 1, 2, 3])
+@pytest.mark.parametrize("what", ["key", "counter"])
+def test_avalanche(orc, gen, what):
+    # Flipping one bit of the stream key or the counter changes each output
+    # bit with probability 1/2 (the avalanche property of §2).
+    rng = np.random.default_rng(11 + gen)
+    flips = []
+    for _ in range(64):
+        key = int(rng.integers(0, 2**63))
+        ctr = int(rng.integers(0, 2**32))
+        bit = int(rng.integers(0, 64 if what == "key" else 32))
+        a = orc.stream_words(gen, key, ctr, 0, 8)
+        if what == "key":
+            b = orc.stream_words(gen, key ^ (1 << bit), ctr, 0, 8)
+        else:
+            b = orc.stream_words(gen, key, ctr ^ (1 << bit), 0, 8)
+        flips.append(_bits(a ^ b).mean())
+    m = float(np.mean(flips))
+    assert abs(m - 0.5) < 5 * 0.5 / math.sqrt(64 * 8 * 32)
+
+
+def test_squares_key_is_odd(orc):
+    for k in [0, 1, 2, 0x5EED, 2**64 - 1, 12345678901234]:
+        assert orc.squares_key(k) & 1 == 1
+
+
+# ------------------------------------------------------------- stream layout -
+
+@pytest.mark.parametrize("gen", [0, 1, 2, 3])
+def test_prefix_and_offset_invariance(orc, gen):
+    full = orc.stream_words(gen, 0xABCDEF, 17, 0, 300)
+    for first, n in [(0, 1), (3, 9), (4, 64), (101, 199), (299, 1)]:
+        assert np.array_equal(orc.stream_words(gen, 0xABCDEF, 17, first, n), full[first:first + n])
+
+
+@pytest.mark.parametrize("gen", [0, 1, 2, 3])
+@pytest.mark.parametrize("dtype", [0, 1, 2, 3])
+def test_fill_rows_are_independent_streams(orc, gen, dtype):
+    # A stream's values depend only on (gen, seed ^ s, counter, j): subsetting
+    # the stream range gives the same rows.
+    a = orc.fill(gen, dtype, 0x5EED, 9, n_streams=40, dps=7)
+    for s in (0, 13, 39):
+        b = orc.fill(gen, dtype, 0x5EED ^ s, 9, n_streams=1, dps=7)
+        c = orc.fill(gen, dtype, 0x5EED, 9, n_streams=1, dps=7, s_first=s)
+        assert np.array_equal(a[s * 7:(s + 1) * 7], b)
+        assert np.array_equal(b, c)
+
+
+def test_fill_prefix_property(orc):
+    for gen in range(4):
+        for dtype in range(4):
+            big = orc.fill(gen, dtype, 1, 2, n_streams=3, dps=12).reshape(3, 12)
+            small = orc.fill(gen, dtype, 1, 2, n_streams=3, dps=8).reshape(3, 8)
+            assert np.array_equal(big[:, :8], small)
+
+
+def test_fill_threads_do_not_change_bits(orc):
+    a = orc.fill(0, 3, 5, 6, n_streams=1000, dps=5)
+    b = orc.fill(0, 3, 5, 6, n_streams=1000, dps=5, threads=4)
+    assert np.array_equal(a, b)
+
+
+def test_word_range_limit(orc):
+    with pytest.raises(ValueError):
+        orc.stream_words(0, 1, 1, 2**32 - 2, 3)
+
+
+# ------------------------------------------------------------------ maps ----
+
+def test_f32_uniform_exact_edges(orc):
+    assert orc.f32_uniform(0) == 0.0
+    assert orc.f32_uniform(0xFF) == 0.0
+    assert orc.f32_uniform(0x100) == 2.0 ** -24
+    assert orc.f32_uniform(0x80000000) == 0.5
+    assert orc.f32_uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    rng = np.random.default_rng(3)
+    for w in rng.integers(0, 2**32, 200, dtype=np.uint64):
+        v = orc.f32_uniform(int(w))
+        assert float(np.float32(v)) == v          # representable in FP32
+        assert Fraction(v) * 2**24 == int(w) >> 8   # exact dyadic value
+
+
+def test_f64_uniform_word_order_and_edges(orc):
+    # The first word is the high half (the paper's Random123 example, Fig. 3).
+    assert orc.f64_uniform(0x80000000, 0) == 0.5
+    assert orc.f64_uniform(0, 0x800) == 2.0 ** -53
+    assert orc.f64_uniform(0, 0x7FF) == 0.0
+    assert orc.f64_uniform(0, 0x80000000) == 2.0 ** -33
+    assert orc.f64_uniform(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+
+
+def test_box_muller_polar_invariants(orc):
+    rng = np.random.default_rng(4)
+    for w0, w1 in rng.integers(0, 2**32, (300, 2), dtype=np.uint64):
+        z0, z1 = orc.box_muller(int(w0), int(w1))
+        u1 = ((int(w0) >> 8) + 1) / 2**24
+        u2 = (int(w1) >> 8) / 2**24
+        r2 = -2.0 * math.log(u1)
+        assert math.isclose(z0 * z0 + z1 * z1, r2, rel_tol=1e-13, abs_tol=1e-300)
+        if r2 > 1e-20:
+            ang = math.atan2(z1, z0) % (2 * math.pi)
+            d = abs(ang - 2 * math.pi * u2)
+            assert min(d, 2 * math.pi - d) < 1e-12
+
+
+def test_box_muller_special_cases(orc):
+    r_max = math.sqrt(-2.0 * math.log(2.0 ** -24))
+    z0, z1 = orc.box_muller(0, 0)                 # u1 = 2^-24, u2 = 0
+    assert math.isclose(z0, r_max, rel_tol=1e-15) and z1 == 0.0
+    z0, z1 = orc.box_muller(0xFFFFFFFF, 12345)    # u1 = 1 -> radius 0
+    assert z0 == 0.0 and z1 == 0.0
+    z0, z1 = orc.box_muller(0, 0x40000000)        # u2 = 1/4 -> pure sine
+    assert abs(z0) < 1e-15 * r_max and math.isclose(z1, r_max, rel_tol=1e-15)
+    assert r_max == pytest.approx(5.76811, abs=1e-5)
+
+
+def test_normals_distribution(orc):
+    from scipy import stats
+
+    z = orc.fill(0, 3, 0x5EED, 0, n_streams=1 << 14, dps=16)
+    n = z.size
+    assert abs(z.mean()) < 5 / math.sqrt(n)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    assert np.abs(z).max() <= math.sqrt(-2 * math.log(2.0 ** -24)) + 1e-12
+
+
+def test_uniform_moments(orc):
+    for dtype in (1, 2):
+        u = orc.fill(1, dtype, 0x5EED, 0, n_streams=1 << 14, dps=16)
+        n = u.size
+        assert u.min() >= 0.0 and u.max() < 1.0
+        assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / n)
+        assert abs(u.var() - 1 / 12) < 5 * math.sqrt(1 / 180 / n)
+
+
+# ----------------------------------------------------------------- walks ----
+
+def _normals(orc, key64, t):
+    blk = orc.philox4x32_10((0, t, 0, 0), (key64 & M32, key64 >> 32))
+    a = orc.box_muller(blk[0], blk[1])
+    b = orc.box_muller(blk[2], blk[3])
+    return a[0], a[1], b[0]
+
+
+def test_walk2d_counter_convention_and_closed_form(orc):
+    # Fig. 1: initial state from counter 0, step `iter` uses counter iter = 1..STEPS.
+    dt, D, steps = np.float32(1e-3), np.float32(1.0), 25
+    s = math.sqrt(2.0 * float(D) * float(dt))
+    x0, xT = orc.walk2d(seed=0, n=6, steps=steps, dt=float(dt), D=float(D), p_first=1000)
+    for i in range(6):
+        pid = 1000 + i
+        blk0 = orc.philox4x32_10((0, 0, 0, 0), (pid, 0))
+        assert x0[i, 0] == (blk0[0] >> 8) / 2**24 and x0[i, 1] == (blk0[1] >> 8) / 2**24
+        zs = [_normals(orc, pid, t)[:2] for t in range(1, steps + 1)]
+        ex = x0[i, 0] + s * math.fsum(z[0] for z in zs)
+        ey = x0[i, 1] + s * math.fsum(z[1] for z in zs)
+        assert abs(xT[i, 0] - ex) < 1e-13 and abs(xT[i, 1] - ey) < 1e-13
+
+
+def test_walk2d_einstein_relation(orc):
+    # Var(x_T - x_0) = 2 D T dt per coordinate for pure diffusion.
+    n, steps, dt, D = 4096, 100, 1e-3, 1.0
+    x0, xT = orc.walk2d(seed=0, n=n, steps=steps, dt=dt, D=D, threads=4)
+    d = (xT - x0).ravel()
+    var_true = 2 * D * steps * float(np.float32(dt))
+    assert abs(d.var() / var_true - 1) < 5 * math.sqrt(2 / d.size)
+    assert abs(d.mean()) < 5 * math.sqrt(var_true / d.size)
+
+
+W3 = dict(steps=40, K=8, dt=float(np.float32(1e-3)), mu=(0.1, -0.2, 0.05), sigma=0.5, k=2.0)
+
+
+def _f32(v):
+    return float(np.float32(v))
+
+
+def test_walk3d_closed_form_and_checkpoints(orc):
+    n, seed = 5, 0
+    x0 = orc.walk3d_init(seed, n, p_first=7)
+    xT, ck = orc.walk3d_forward(seed, n, W3["steps"], W3["K"], W3["dt"], W3["mu"], W3["sigma"],
+                                p_first=7, want_ckpt=True)
+    dt, sg = W3["dt"], _f32(W3["sigma"])
+    mu = [_f32(m) for m in W3["mu"]]
+    for i in range(n):
+        pid = 7 + i
+        blk0 = orc.philox4x32_10((0, 0, 0, 0), (pid, 0))
+        assert list(x0[i]) == [2 * (w >> 8) / 2**24 - 1 for w in blk0[:3]]
+        zs = [_normals(orc, pid, t + 1) for t in range(W3["steps"])]
+        for c in range(3):
+            ex = x0[i, c] + W3["steps"] * mu[c] * dt + sg * math.sqrt(dt) * math.fsum(z[c] for z in zs)
+            assert abs(xT[i, c] - ex) < 1e-12
+            for j in range(ck.shape[0]):
+                t = j * W3["K"]
+                ej = x0[i, c] + t * mu[c] * dt + sg * math.sqrt(dt) * math.fsum(z[c] for z in zs[:t])
+                assert abs(ck[j, i, c] - ej) < 1e-12
+
+
+def _loss_at(orc, n, mu, sigma, x0=None, P=None):
+    xT, _ = orc.walk3d_forward(0, n, W3["steps"], W3["K"], W3["dt"], mu, sigma, x0=x0)
+    return orc.walk3d_loss(xT, W3["k"], P or n)
+
+
+def test_walk3d_adjoint_vs_central_differences(orc):
+    # The loss is quadratic in (mu, sigma, x0), so central differences with
+    # h = 1e-3 are exact up to FP64 rounding.
+    n = 6
+    x0 = orc.walk3d_init(0, n)
+    xT, _ = orc.walk3d_forward(0, n, W3["steps"], W3["K"], W3["dt"], W3["mu"], W3["sigma"], x0=x0)
+    dmu, dsig, dx0 = orc.walk3d_adjoint(0, n, W3["steps"], W3["dt"], xT, W3["k"], n)
+    h = 1e-3
+    # d/dx0: the forward takes x0 as FP64 input, so the perturbation is exact.
+    for i in (0, 3):
+        for c in range(3):
+            xp, xm = x0.copy(), x0.copy()
+            xp[i, c] += h
+            xm[i, c] -= h
+            fd = (_loss_at(orc, n, W3["mu"], W3["sigma"], xp) - _loss_at(orc, n, W3["mu"], W3["sigma"], xm)) / (2 * h)
+            assert fd == pytest.approx(dx0[i, c], rel=1e-7, abs=1e-10)
+    # d/dmu and d/dsigma: the parameters cross the C interface as FP32, so
+    # perturb by h rounded to the FP32 grid around the value and divide by the
+    # actual step taken.
+    for c in range(3):
+        mp, mm = list(W3["mu"]), list(W3["mu"])
+        mp[c] = _f32(_f32(mp[c]) + h)
+        mm[c] = _f32(_f32(mm[c]) - h)
+        fd = (_loss_at(orc, n, mp, W3["sigma"], x0) - _loss_at(orc, n, mm, W3["sigma"], x0)) / (mp[c] - mm[c])
+        assert fd == pytest.approx(dmu[c], rel=1e-7)
+    sp, sm = _f32(_f32(W3["sigma"]) + h), _f32(_f32(W3["sigma"]) - h)
+    fd = (_loss_at(orc, n, W3["mu"], sp, x0) - _loss_at(orc, n, W3["mu"], sm, x0)) / (sp - sm)
+    assert fd == pytest.approx(dsig, rel=1e-7)
+
+
+def test_walk3d_adjoint_closed_form(orc):
+    # Linear walk: dL/dmu = k T dt mean(x_T), dL/dsigma = k sqrt(dt) mean(x_T . S_p)
+    # with S_p the sum of the particle's normals, dL/dx0 = k x_T / P.
+    n, k = 4, W3["k"]
+    xT, _ = orc.walk3d_forward(0, n, W3["steps"], W3["K"], W3["dt"], W3["mu"], W3["sigma"])
+    dmu, dsig, dx0 = orc.walk3d_adjoint(0, n, W3["steps"], W3["dt"], xT, k, n)
+    assert np.allclose(dmu, k * W3["steps"] * W3["dt"] * xT.mean(axis=0), rtol=1e-12)
+    S = np.array([[math.fsum(_normals(orc, p, t + 1)[c] for t in range(W3["steps"])) for c in range(3)]
+                  for p in range(n)])
+    assert dsig == pytest.approx(k * math.sqrt(W3["dt"]) * float((xT * S).sum()) / n, rel=1e-12)
+    assert np.allclose(dx0, k * xT / n, rtol=0, atol=1e-15)
+    assert orc.walk3d_loss(xT, k, n) == pytest.approx(0.5 * k * float((xT ** 2).sum()) / n, rel=1e-14)
