@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the counter-based generation hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl orand|reference]
+
+One JSON line on rank 0.  `value` is the headline metric: Philox4x32-10 u32
+bulk-fill throughput (GB/s of output written) on the 2^24-stream x 16-draw
+workload (1 GiB per fill; far larger than the 126 MB L2, so no flush is
+needed between launches).  A timed step is one pass over every hot-path row
+that is built; each row is timed with CUDA events on the stream its kernels
+run on, and the row table rides along in `rows`.
+
+--impl reference times the CPU oracle (the plain C restatement of the
+method) on the host cores for the same metric, on a bounded sample of the
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6400.0
+METRIC = "Philox u32 fill GB/s vs HBM peak; walk particle-steps/s; adjoint vs plain walk"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["orand", "reference"], default="orand")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="", help="keep only rows whose name contains this text (profiling)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash(paths):
+    h = hashlib.sha1()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel_key, src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel_key and parts[1] == src_hash:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid):
+        self.uuid = device_uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.uuid, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sms.append(float(f[0]))
+                maxs.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxs) if maxs else None, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# --------------------------------------------------------------------- rows --
+
+class Row:
+    """One hot-path row: `run(stream_handle)` launches its kernels on the
+    given stream; `units` of `unit` are processed per run."""
+
+    def __init__(self, name, run, units, unit, kernels, bytes_written=None):
+        self.name, self.run, self.units, self.unit, self.kernels = name, run, units, unit, kernels
+        self.bytes_written = bytes_written
+        self.times_ms = []
+
+
+def fill_rows(torch, orand, W, rank):
+    rows = []
+    c = W.FILL_LARGE
+    n_streams, dps = c["n_streams"], c["dps"]
+    seed = c["seed"] ^ (rank * n_streams)   # rank r owns global streams [r*2^24, (r+1)*2^24)
+    bufs = {}
+    for dt in (W.U32, W.F32_UNIFORM, W.F64_UNIFORM, W.F32_NORMAL):
+        bufs[dt] = torch.empty(n_streams * dps, dtype=orand.torch_dtype(dt), device="cuda")
+    for gen in (W.PHILOX, W.THREEFRY, W.SQUARES, W.TYCHE):
+        for dt in (W.U32, W.F32_UNIFORM, W.F64_UNIFORM, W.F32_NORMAL):
+            out = bufs[dt]
+            nbytes = out.numel() * out.element_size()
+
+            def run(sh, gen=gen, dt=dt, out=out):
+                orand.orand_fill(gen, dt, seed, c["counter"], n_streams, dps, out.data_ptr(), sh)
+
+            rows.append(Row("fill/%s/%s" % (W.GEN_NAMES[gen], W.DTYPE_NAMES[dt]), run, nbytes, "B", 1,
+                            bytes_written=nbytes))
+    return rows, bufs
+
+
+# ---------------------------------------------------------------- reference --
+
+def cpu_oracle_fill_rate(threads, n_streams=1 << 21, dps=16):
+    """Oracle Philox u32 fill on `threads` host threads: returns (GB/s, seconds, sample)."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    out = oracle.fill(0, 0, 0x5EED, 0, n_streams, dps, threads=threads)
+    dt = time.perf_counter() - t0
+    return out.nbytes / dt / 1e9, dt, "philox4x32_10 u32, %d streams x %d draws (%d MiB), seed 0x5EED" % (
+        n_streams, dps, out.nbytes >> 20)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    vals = []
+    for _ in range(max(args.warmup, 0)):
+        cpu_oracle_fill_rate(threads, n_streams=1 << 18)
+    t_total = 0.0
+    sample = None
+    for _ in range(args.steps):
+        v, dt, sample = cpu_oracle_fill_rate(threads, n_streams=1 << 20)
+        vals.append(v)
+        t_total += dt
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "philox4x32_10 u32 bulk fill, seed 0x5EED, counter 0, 16 draws per stream; "
+                               "CPU oracle on a 2^20-stream sample of the 2^24-stream workload"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# -------------------------------------------------------------------- main --
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    import paper_2310_19925_b300 as orand
+    from paper_2310_19925_b300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    orand._lib()
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    rows, _keep = fill_rows(torch, orand, W, rank)
+    head = rows[0]  # fill/philox4x32_10/u32: the headline kernel
+    if args.only:
+        rows = [r for r in rows if args.only in r.name]
+        if head not in rows:
+            rows.insert(0, head)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        for r in rows:
+            r.run(sh)
+    barrier()
+
+    props = torch.cuda.get_device_properties(local_rank)
+    sampler = ClockSampler("GPU-" + str(props.uuid)) if hasattr(props, "uuid") else ClockSampler("0")
+    sampler.start()
+    time.sleep(0.3)
+    ev = []
+    step_start = torch.cuda.Event(enable_timing=True)
+    step_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    step_start.record()
+    for _ in range(args.steps):
+        for r in rows:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            r.run(sh)
+            b.record()
+            ev.append((r, a, b))
+    step_end.record()
+    barrier()
+    clocks = sampler.stop()
+    for r, a, b in ev:
+        r.times_ms.append(a.elapsed_time(b))
+    total_ms = step_start.elapsed_time(step_end)
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    head_ms = max_over_ranks(statistics.mean(head.times_ms))
+    ms_per_step = max_over_ranks(total_ms / args.steps)
+    value = world * head.units / (head_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    achieved = head.bytes_written / (statistics.mean(head.times_ms) * 1e-3) / 1e9
+    src = source_hash(["paper_2310_19925_b300/csrc/fill.cu", "include/orand_device.cuh"])
+    traffic = ncu_traffic("fill_random_access_kernel<0,0,1>", src)
+
+    row_table = {}
+    for r in rows:
+        t = max_over_ranks(statistics.mean(r.times_ms))
+        e = {"ms": round(t, 4), "unit_per_s": world * r.units / (t * 1e-3)}
+        if r.bytes_written:
+            e["GB/s"] = round(world * r.bytes_written / (t * 1e-3) / 1e9, 1)
+            e["frac_hbm"] = round(r.bytes_written / (t * 1e-3) / 1e9 / peak, 4)
+        row_table[r.name] = e
+
+    # End to end through the C ABI: the same fill, then the 1 GiB result read
+    # back into pinned host memory, both inside the timed region.
+    host = torch.empty(head.bytes_written // 4, dtype=torch.int32, pin_memory=True)
+    dev_out = _keep[W.U32]
+    e2e_ms = []
+    for i in range(max(2, min(args.steps, 5)) + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        head.run(sh)
+        host.copy_(dev_out, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        if i:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_t = max_over_ranks(statistics.mean(e2e_ms))
+    e2e = {"value": world * head.bytes_written / (e2e_t * 1e-3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": head.bytes_written}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        v, dt, sample = cpu_oracle_fill_rate(threads)
+        cpu = {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "philox4x32_10 u32 bulk fill, 2^24 streams x 16 draws per rank (1 GiB), "
+                                   "key = stream id ^ 0x5EED, counter 0",
+                       "step": "one pass over every built hot-path row (%d rows)" % len(rows),
+                       "l2": "every output >= 1 GiB, larger than the 126 MB L2: no flush between launches",
+                       "parallelism": "dp%d (disjoint stream ranges per rank)" % world},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "fill_random_access_kernel<philox,u32,vec>",
+                         "peak_kind": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"},
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": sum(r.kernels for r in rows) * args.steps,
+            "rows": row_table,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,338 @@
+/*
+ * orand_device.cuh -- in-thread counter-based generation for CUDA kernels
+ * (sm_103a).  Header-only; include it from any .cu file to draw random
+ * numbers inside your own kernels with no generator state in memory.
+ *
+ * This is the device half of the OpenRAND method (arXiv 2310.19925): a
+ * generator is built from a 64-bit seed and a 32-bit counter (§3), its state
+ * fits in registers (§2: 96 bits of user state), and the same (seed,
+ * counter) gives the same stream on every thread count and launch shape.
+ * The paper's usage pattern (Fig. 1) reads, with this header:
+ *
+ *     orand::Philox rng(p.pid, counter);
+ *     float2 r = rng.uniform2_f32();
+ *
+ * Generator definitions follow the publications the paper cites for them
+ * (§3): Philox4x32-10 and Threefry4x32-20 (Salmon et al., SC'11), Squares
+ * (Widynski 2020), Tyche (Neves & Araujo 2011).  Stream layout, shared by
+ * every kernel of the library so that all delivery paths emit identical bits:
+ *
+ *   Philox    key = (lo32(key64), hi32(key64)), counter block
+ *             (b, counter, 0, 0); words 4b..4b+3 are its lanes 0..3.
+ *   Threefry  key = (lo32, hi32, 0, 0); same counter block layout.
+ *   Squares   word w = squares32((counter << 32) | w, fmix64(key64) | 1).
+ *   Tyche     a = hi32(key64), b = lo32(key64), c = 2654435769,
+ *             d = 1367130551 ^ counter, 20 MIX; word w = b after MIX w+1.
+ *
+ * Maps: FP32 uniform (w >> 8) * 2^-24; FP64 uniform from two words, first
+ * one high (Fig. 3), ((hi:lo) >> 11) * 2^-53, built with integer ops only;
+ * Box-Muller with u1 = ((w0>>8)+1) * 2^-24, u2 = (w1>>8) * 2^-24,
+ * r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2) via sincospif.
+ */
+#pragma once
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace orand {
+
+/* ---------------------------------------------------------------- Philox */
+
+constexpr uint32_t PHILOX_M0 = 0xD2511F53u;
+constexpr uint32_t PHILOX_M1 = 0xCD9E8D57u;
+constexpr uint32_t PHILOX_W0 = 0x9E3779B9u;  /* floor(2^32 / golden ratio) */
+constexpr uint32_t PHILOX_W1 = 0xBB67AE85u;  /* floor(2^32 (sqrt(3) - 1)) */
+
+/* One Philox round on (c0..c3) with round key (k0, k1).  The 64-bit
+ * products map to one wide integer multiply-add each. */
+__device__ __forceinline__ void philox_round(uint32_t &c0, uint32_t &c1, uint32_t &c2,
+                                             uint32_t &c3, uint32_t k0, uint32_t k1)
+{
+    const uint64_t p0 = (uint64_t)PHILOX_M0 * c0;
+    const uint64_t p1 = (uint64_t)PHILOX_M1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+}
+
+/* Stateless Philox4x32-10 block function. */
+__device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key)
+{
+    uint32_t c0 = ctr.x, c1 = ctr.y, c2 = ctr.z, c3 = ctr.w;
+    uint32_t k0 = key.x, k1 = key.y;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        philox_round(c0, c1, c2, c3, k0, k1);
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+/* Philox with the ten round keys precomputed once per stream (a fill
+ * thread reuses them for every block of the same key). */
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+    __device__ __forceinline__ explicit PhiloxKeys(uint64_t key64)
+    {
+        uint32_t a = (uint32_t)key64, b = (uint32_t)(key64 >> 32);
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            k0[r] = a; k1[r] = b;
+            a += PHILOX_W0; b += PHILOX_W1;
+        }
+    }
+    __device__ __forceinline__ uint4 block(uint32_t b_idx, uint32_t counter) const
+    {
+        uint32_t c0 = b_idx, c1 = counter, c2 = 0u, c3 = 0u;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) philox_round(c0, c1, c2, c3, k0[r], k1[r]);
+        return make_uint4(c0, c1, c2, c3);
+    }
+};
+
+__device__ __forceinline__ uint4 philox_block(uint64_t key64, uint32_t counter, uint32_t b_idx)
+{
+    return philox4x32_10(make_uint4(b_idx, counter, 0u, 0u),
+                         make_uint2((uint32_t)key64, (uint32_t)(key64 >> 32)));
+}
+
+/* -------------------------------------------------------------- Threefry */
+
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int r) { return __funnelshift_l(x, x, r); }
+
+template <int RA, int RB, bool EVEN>
+__device__ __forceinline__ void threefry_round(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3)
+{
+    if (EVEN) {
+        x0 += x1; x1 = rotl32(x1, RA) ^ x0;
+        x2 += x3; x3 = rotl32(x3, RB) ^ x2;
+    } else {
+        x0 += x3; x3 = rotl32(x3, RA) ^ x0;
+        x2 += x1; x1 = rotl32(x1, RB) ^ x2;
+    }
+}
+
+/* Four rounds starting at row R0 of the rotation table, then injection I. */
+template <int R0, int I>
+__device__ __forceinline__ void threefry_quad(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
+                                              const uint32_t ks[5])
+{
+    constexpr int ROT[8][2] = {{10, 26}, {11, 21}, {13, 27}, {23, 5},
+                               {6, 20},  {17, 11}, {25, 10}, {18, 20}};
+    threefry_round<ROT[R0 + 0][0], ROT[R0 + 0][1], true>(x0, x1, x2, x3);
+    threefry_round<ROT[R0 + 1][0], ROT[R0 + 1][1], false>(x0, x1, x2, x3);
+    threefry_round<ROT[R0 + 2][0], ROT[R0 + 2][1], true>(x0, x1, x2, x3);
+    threefry_round<ROT[R0 + 3][0], ROT[R0 + 3][1], false>(x0, x1, x2, x3);
+    x0 += ks[(I + 0) % 5];
+    x1 += ks[(I + 1) % 5];
+    x2 += ks[(I + 2) % 5];
+    x3 += ks[(I + 3) % 5] + (uint32_t)I;
+}
+
+/* Stateless Threefry4x32-20 block function. */
+__device__ __forceinline__ uint4 threefry4x32_20(uint4 ctr, uint4 key)
+{
+    uint32_t ks[5];
+    ks[0] = key.x; ks[1] = key.y; ks[2] = key.z; ks[3] = key.w;
+    ks[4] = 0x1BD11BDAu ^ key.x ^ key.y ^ key.z ^ key.w;
+    uint32_t x0 = ctr.x + ks[0], x1 = ctr.y + ks[1], x2 = ctr.z + ks[2], x3 = ctr.w + ks[3];
+    threefry_quad<0, 1>(x0, x1, x2, x3, ks);
+    threefry_quad<4, 2>(x0, x1, x2, x3, ks);
+    threefry_quad<0, 3>(x0, x1, x2, x3, ks);
+    threefry_quad<4, 4>(x0, x1, x2, x3, ks);
+    threefry_quad<0, 5>(x0, x1, x2, x3, ks);
+    return make_uint4(x0, x1, x2, x3);
+}
+
+__device__ __forceinline__ uint4 threefry_block(uint64_t key64, uint32_t counter, uint32_t b_idx)
+{
+    return threefry4x32_20(make_uint4(b_idx, counter, 0u, 0u),
+                           make_uint4((uint32_t)key64, (uint32_t)(key64 >> 32), 0u, 0u));
+}
+
+/* --------------------------------------------------------------- Squares */
+
+/* x*x + y modulo 2^64 from 32-bit halves: one wide multiply-add for the low
+ * product plus y, one multiply-add for the cross term 2*xl*xh. */
+__device__ __forceinline__ uint64_t sq_add(uint64_t x, uint64_t y)
+{
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
+    const uint64_t p = (uint64_t)xl * xl + y;
+    const uint32_t hi = (uint32_t)(p >> 32) + xl * (xh << 1);
+    return ((uint64_t)hi << 32) | (uint32_t)p;
+}
+
+__device__ __forceinline__ uint64_t swap_halves(uint64_t v) { return (v >> 32) | (v << 32); }
+
+__device__ __forceinline__ uint32_t squares32(uint64_t ctr, uint64_t key)
+{
+    uint64_t x = ctr * key;
+    const uint64_t y = x, z = y + key;
+    x = swap_halves(sq_add(x, y));
+    x = swap_halves(sq_add(x, z));
+    x = swap_halves(sq_add(x, y));
+    return (uint32_t)(sq_add(x, z) >> 32);
+}
+
+/* Per-stream Squares key: MurmurHash3's 64-bit finaliser, forced odd. */
+__device__ __forceinline__ uint64_t squares_key(uint64_t key64)
+{
+    uint64_t h = key64;
+    h ^= h >> 33;
+    h *= 0xFF51AFD7ED558CCDull;
+    h ^= h >> 33;
+    h *= 0xC4CEB9FE1A85EC53ull;
+    h ^= h >> 33;
+    return h | 1ull;
+}
+
+/* Four consecutive Squares words 4b..4b+3 of stream (key, counter). */
+__device__ __forceinline__ uint4 squares_block(uint64_t sq_key, uint32_t counter, uint32_t b_idx)
+{
+    const uint64_t base = ((uint64_t)counter << 32) | ((uint64_t)b_idx << 2);
+    return make_uint4(squares32(base, sq_key), squares32(base + 1, sq_key),
+                      squares32(base + 2, sq_key), squares32(base + 3, sq_key));
+}
+
+/* ----------------------------------------------------------------- Tyche */
+
+struct TycheState {
+    uint32_t a, b, c, d;
+};
+
+__device__ __forceinline__ void tyche_mix(TycheState &s)
+{
+    s.a += s.b; s.d = __byte_perm(s.d ^ s.a, 0, 0x1032);   /* rotl 16 */
+    s.c += s.d; s.b = rotl32(s.b ^ s.c, 12);
+    s.a += s.b; s.d = __byte_perm(s.d ^ s.a, 0, 0x2103);   /* rotl 8 */
+    s.c += s.d; s.b = rotl32(s.b ^ s.c, 7);
+}
+
+__device__ __forceinline__ TycheState tyche_init(uint64_t key64, uint32_t counter)
+{
+    TycheState s;
+    s.a = (uint32_t)(key64 >> 32);
+    s.b = (uint32_t)key64;
+    s.c = 2654435769u;                 /* floor(2^32 / golden ratio) */
+    s.d = 1367130551u ^ counter;       /* floor(2^32 / pi) */
+#pragma unroll 4
+    for (int i = 0; i < 20; ++i) tyche_mix(s);
+    return s;
+}
+
+__device__ __forceinline__ uint32_t tyche_next(TycheState &s)
+{
+    tyche_mix(s);
+    return s.b;
+}
+
+/* ------------------------------------------------------------------ maps */
+
+/* (w >> 8) * 2^-24: exact, in [0, 1 - 2^-24]. */
+__device__ __forceinline__ float u01_f32(uint32_t w)
+{
+    return __uint2float_rn(w >> 8) * 0x1p-24f;
+}
+
+/* ((hi:lo) >> 11) * 2^-53, exact, in [0, 1).  Built from integer ops
+ * (leading-zero count, shift, exponent insert) rather than an integer to
+ * FP64 conversion. */
+__device__ __forceinline__ double u01_f64(uint32_t hi, uint32_t lo)
+{
+    const uint64_t m = ((((uint64_t)hi) << 32) | lo) >> 11;    /* < 2^53 */
+    if (m == 0) return 0.0;
+    const int top = 63 - __clzll((long long)m);                /* 0..52 */
+    const uint64_t mant = (m << (52 - top)) & 0x000FFFFFFFFFFFFFull;
+    const uint64_t expo = (uint64_t)(top - 53 + 1023);
+    return __longlong_as_double((long long)((expo << 52) | mant));
+}
+
+/* Box-Muller pair from two words (accurate logf/sqrtf/sincospif). */
+__device__ __forceinline__ float2 box_muller_f32(uint32_t w0, uint32_t w1)
+{
+    const float u1 = __uint2float_rn((w0 >> 8) + 1u) * 0x1p-24f;   /* (0, 1] */
+    const float two_u2 = __uint2float_rn(w1 >> 8) * 0x1p-23f;       /* [0, 2) */
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(two_u2, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+/* ------------------------------------------------ engine-style generators */
+
+/* Sequential draw interface of the paper's API (§3): construct from
+ * (seed, counter), then draw words and values in order.  The random-access
+ * generators keep a 4-word buffer; Tyche keeps its 4-word state. */
+class Philox {
+  public:
+    __device__ __forceinline__ Philox(uint64_t seed, uint32_t counter)
+        : key_(seed), counter_(counter), blk_(0), lane_(4) {}
+    __device__ __forceinline__ uint32_t operator()()
+    {
+        if (lane_ == 4) { buf_ = philox_block(key_, counter_, blk_++); lane_ = 0; }
+        const uint32_t w = lane_ == 0 ? buf_.x : lane_ == 1 ? buf_.y : lane_ == 2 ? buf_.z : buf_.w;
+        ++lane_;
+        return w;
+    }
+    __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
+    __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
+    __device__ __forceinline__ float2 uniform2_f32() { float a = uniform_f32(); return make_float2(a, uniform_f32()); }
+    __device__ __forceinline__ double2 uniform2_f64() { double a = uniform_f64(); return make_double2(a, uniform_f64()); }
+    __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
+
+  private:
+    uint64_t key_;
+    uint32_t counter_, blk_, lane_;
+    uint4 buf_;
+};
+
+class Threefry {
+  public:
+    __device__ __forceinline__ Threefry(uint64_t seed, uint32_t counter)
+        : key_(seed), counter_(counter), blk_(0), lane_(4) {}
+    __device__ __forceinline__ uint32_t operator()()
+    {
+        if (lane_ == 4) { buf_ = threefry_block(key_, counter_, blk_++); lane_ = 0; }
+        const uint32_t w = lane_ == 0 ? buf_.x : lane_ == 1 ? buf_.y : lane_ == 2 ? buf_.z : buf_.w;
+        ++lane_;
+        return w;
+    }
+    __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
+    __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
+    __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
+
+  private:
+    uint64_t key_;
+    uint32_t counter_, blk_, lane_;
+    uint4 buf_;
+};
+
+class Squares {
+  public:
+    __device__ __forceinline__ Squares(uint64_t seed, uint32_t counter)
+        : key_(squares_key(seed)), ctr_((uint64_t)counter << 32) {}
+    __device__ __forceinline__ uint32_t operator()() { return squares32(ctr_++, key_); }
+    __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
+    __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
+    __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
+
+  private:
+    uint64_t key_, ctr_;
+};
+
+class Tyche {
+  public:
+    __device__ __forceinline__ Tyche(uint64_t seed, uint32_t counter) : s_(tyche_init(seed, counter)) {}
+    __device__ __forceinline__ uint32_t operator()() { return tyche_next(s_); }
+    __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
+    __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
+    __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
+
+  private:
+    TycheState s_;
+};
+
+}  // namespace orand

@@ -1,0 +1,79 @@
+// Library-wide C ABI pieces: status strings, version, per-thread last CUDA
+// error, cached device properties.
+#include <atomic>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace orand_impl {
+
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+
+namespace {
+constexpr int kMaxDevices = 64;
+struct DeviceCache {
+    std::once_flag once[kMaxDevices];
+    DeviceInfo info[kMaxDevices];
+    orand_status_t status[kMaxDevices];
+};
+DeviceCache &device_cache()
+{
+    static DeviceCache c;
+    return c;
+}
+}  // namespace
+
+orand_status_t current_device(DeviceInfo *info)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kMaxDevices) return ORAND_ERR_UNSUPPORTED;
+    DeviceCache &c = device_cache();
+    std::call_once(c.once[dev], [&]() {
+        DeviceInfo d{};
+        d.device = dev;
+        orand_status_t st = ORAND_OK;
+        if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.cc_major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.max_threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) !=
+                cudaSuccess) {
+            set_last_cuda_error(cudaGetLastError());
+            st = ORAND_ERR_CUDA;
+        } else if (d.cc_major != 10 || d.cc_minor != 3) {
+            st = ORAND_ERR_UNSUPPORTED;
+        }
+        c.info[dev] = d;
+        c.status[dev] = st;
+    });
+    *info = c.info[dev];
+    return c.status[dev];
+}
+
+}  // namespace orand_impl
+
+extern "C" {
+
+const char *orand_status_string(orand_status_t status)
+{
+    switch (status) {
+    case ORAND_OK: return "ORAND_OK";
+    case ORAND_ERR_INVALID_ARG: return "ORAND_ERR_INVALID_ARG: null pointer, unknown enum or bad field";
+    case ORAND_ERR_OVERFLOW: return "ORAND_ERR_OVERFLOW: size overflows, or a stream needs more than 2^32 words";
+    case ORAND_ERR_ALIGNMENT: return "ORAND_ERR_ALIGNMENT: pointer or offset not aligned to its element size";
+    case ORAND_ERR_ALLOC: return "ORAND_ERR_ALLOC: context allocation failed";
+    case ORAND_ERR_CUDA: return "ORAND_ERR_CUDA: CUDA runtime call or launch failed";
+    case ORAND_ERR_DEVICE_TIMEOUT: return "ORAND_ERR_DEVICE_TIMEOUT: a device-side wait gave up";
+    case ORAND_ERR_UNSUPPORTED: return "ORAND_ERR_UNSUPPORTED: device is not compute capability 10.3 (sm_103a)";
+    }
+    return "ORAND: unknown status";
+}
+
+int orand_version(void) { return 100; }
+
+cudaError_t orand_last_cuda_error(void) { return orand_impl::g_last_cuda_error; }
+
+}  // extern "C"

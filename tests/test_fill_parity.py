@@ -1,0 +1,145 @@
+"""GPU parity of the bulk fills against the CPU oracle.
+
+Bar: u32 words, FP32 and FP64 uniforms bit-exact; FP32 normals within 4 ulp
+(ordered-integer distance) of the FP64 oracle value rounded to FP32.  Small
+shapes span several groups, ragged tails and both store paths; the full
+2^24 x 16 workload runs in the benchmark's launch configuration and is
+checked on sampled streams plus whole-array properties.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import to_numpy, ulp_distance_f32
+
+import paper_2310_19925_b300 as orand
+from paper_2310_19925_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GENS = [W.PHILOX, W.THREEFRY, W.SQUARES, W.TYCHE]
+DTYPES = [W.U32, W.F32_UNIFORM, W.F64_UNIFORM, W.F32_NORMAL]
+NORMAL_ULP = 4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def compare(dtype, gpu, ref):
+    if dtype == W.F32_NORMAL:
+        d = ulp_distance_f32(gpu, ref)
+        assert d.max(initial=0) <= NORMAL_ULP, "max ulp %d" % d.max()
+    elif dtype == W.F32_UNIFORM:
+        assert np.array_equal(gpu.astype(np.float64), ref)
+    else:
+        assert np.array_equal(gpu, ref)
+
+
+def gpu_fill(torch, gen, dtype, seed, counter, n_streams, dps, offset_elems=0):
+    n = n_streams * dps
+    buf = torch.full((n + offset_elems + 4,), -7, dtype=orand.torch_dtype(dtype), device="cuda")
+    out = buf[offset_elems:offset_elems + n]
+    orand.fill(gen, dtype, seed, counter, n_streams, dps, out=out)
+    torch.cuda.synchronize()
+    # canaries around the output stay untouched
+    assert bool((buf[:offset_elems] == -7).all()) and bool((buf[offset_elems + n:] == -7).all())
+    return to_numpy(out)
+
+
+SHAPES = [(1, 1), (3, 5), (257, 4), (100, 16), (33, 67), (1000, 8), (5, 130)]
+
+
+@pytest.mark.parametrize("gen", GENS)
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fill_small_shapes(torch_cuda, orc, gen, dtype, shape):
+    n_streams, dps = shape
+    for seed, counter in [(0x5EED, 0), (2**64 - 1, 0xFFFFFFFF)]:
+        ref = orc.fill(gen, dtype, seed, counter, n_streams, dps)
+        got = gpu_fill(torch_cuda, gen, dtype, seed, counter, n_streams, dps)
+        compare(dtype, got, ref)
+
+
+@pytest.mark.parametrize("gen", GENS)
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fill_unaligned_output_takes_scalar_path(torch_cuda, orc, gen, dtype):
+    # One element past a 16-byte boundary: element-aligned, not vector-aligned.
+    ref = orc.fill(gen, dtype, 99, 3, 300, 16)
+    got = gpu_fill(torch_cuda, gen, dtype, 99, 3, 300, 16, offset_elems=1)
+    compare(dtype, got, ref)
+
+
+@pytest.mark.parametrize("dtype", [W.U32, W.F32_UNIFORM])
+def test_fill_small_workload_full(torch_cuda, orc, dtype):
+    c = W.FILL_SMALL
+    ref = orc.fill(W.PHILOX, dtype, c["seed"], c["counter"], c["n_streams"], c["dps"], threads=8)
+    got = gpu_fill(torch_cuda, W.PHILOX, dtype, c["seed"], c["counter"], c["n_streams"], c["dps"])
+    compare(dtype, got, ref)
+
+
+def test_fill_typed_entry_points_agree(torch_cuda):
+    torch = torch_cuda
+    s = torch.cuda.current_stream().cuda_stream
+    for dtype, fn in [(W.U32, orand.orand_fill_u32), (W.F32_UNIFORM, orand.orand_fill_uniform_f32),
+                      (W.F64_UNIFORM, orand.orand_fill_uniform_f64), (W.F32_NORMAL, orand.orand_fill_normal_f32)]:
+        a = torch.empty(4096, dtype=orand.torch_dtype(dtype), device="cuda")
+        b = torch.empty_like(a)
+        fn(W.THREEFRY, 5, 6, 64, 64, a.data_ptr(), s)
+        orand.orand_fill(W.THREEFRY, dtype, 5, 6, 64, 64, b.data_ptr(), s)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
+def test_fill_is_independent_of_stream_range_split(torch_cuda):
+    # Streams [s0, s0 + n) with s0 a multiple of a power of two >= n are the
+    # streams 0..n-1 of seed ^ s0 (key64 = seed ^ s): how ranks shard a fill.
+    torch = torch_cuda
+    seed, n = 0x5EED, 1 << 10
+    full = orand.fill(W.SQUARES, W.U32, seed, 0, 4 * n, 16)
+    for r in range(4):
+        part = orand.fill(W.SQUARES, W.U32, seed ^ (r * n), 0, n, 16)
+        assert torch.equal(full[r * n * 16:(r + 1) * n * 16], part)
+
+
+@pytest.mark.parametrize("gen", GENS)
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fill_large_workload_sampled(torch_cuda, orc, gen, dtype):
+    """The benchmark's 2^24 x 16 fill, exact on sampled streams plus range and moments on all values."""
+    torch = torch_cuda
+    c = W.FILL_LARGE
+    n_streams, dps = c["n_streams"], c["dps"]
+    out = orand.fill(gen, dtype, c["seed"], c["counter"], n_streams, dps)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1000 + 4 * gen + dtype)
+    streams = np.unique(np.concatenate([[0, 1, n_streams - 1], rng.integers(0, n_streams, 1024)]))
+    idx = torch.as_tensor((streams[:, None] * dps + np.arange(dps)[None, :]).ravel(), device="cuda")
+    got = to_numpy(out[idx]).reshape(len(streams), dps)
+    for i, s in enumerate(streams):
+        ref = orc.fill(gen, dtype, c["seed"], c["counter"], 1, dps, s_first=int(s))
+        compare(dtype, got[i], ref)
+    n = out.numel()
+    if dtype == W.F32_UNIFORM:
+        assert out.min().item() >= 0.0 and out.max().item() <= 1.0 - 2.0 ** -24
+    if dtype in (W.F32_UNIFORM, W.F64_UNIFORM):
+        x = out.double()
+        assert abs(x.mean().item() - 0.5) < 5 * math.sqrt(1 / 12 / n)
+        assert out.max().item() < 1.0
+    if dtype == W.F32_NORMAL:
+        x = out.double()
+        assert x.abs().max().item() <= 5.7682
+        assert abs(x.mean().item()) < 5 / math.sqrt(n)
+        assert abs(x.var().item() - 1) < 5 * math.sqrt(2 / n)
+    if dtype == W.U32:
+        w = out.view(torch.int32)
+        top = ((w >> 24) & 0xFF).bincount(minlength=256).double()
+        chi2 = ((top - n / 256) ** 2 / (n / 256)).sum().item()
+        assert abs(chi2 - 255) < 5 * math.sqrt(2 * 255)
+    del out
+    torch.cuda.empty_cache()
