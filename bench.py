@@ -154,6 +154,83 @@ def fill_rows(torch, orand, W, rank):
     return rows, bufs
 
 
+def walk_rows(torch, orand, W, rank):
+    """Fused 2D walk (particle-steps) and fused 3D forward + adjoint."""
+    rows = []
+    keep = {}
+    c2 = W.WALK2D
+    P2 = c2["n_particles"]
+    pos = torch.empty((P2, 2), dtype=torch.float32, device="cuda")
+    keep["pos"] = pos
+    prm2 = orand.walk2d_params(P2, c2["steps"], c2["dt"], c2["D"], c2["seed"], p_first=rank * P2)
+
+    def run2(sh):
+        orand.orand_brownian_walk(prm2, pos.data_ptr(), sh)
+
+    rows.append(Row("walk2d/fused", run2, P2 * c2["steps"], "particle-steps", 1))
+
+    c3 = W.WALK3D
+    P3, T = c3["n_particles"], c3["steps"]
+    prm3 = orand.walk3d_params(P3, T, c3["dt"], c3["mu"], c3["sigma"], c3["k"], c3["seed"], c3["ckpt_every"],
+                               p_first=rank * P3, p_total=P3)
+    ctx = orand.default_context().handle
+    xT = torch.empty((P3, 3), dtype=torch.float32, device="cuda")
+    ck = torch.empty((orand.n_checkpoints(T, c3["ckpt_every"]), P3, 3), dtype=torch.float32, device="cuda")
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    dmu = torch.empty(3, dtype=torch.float64, device="cuda")
+    dsig = torch.empty((), dtype=torch.float64, device="cuda")
+    dx0 = torch.empty_like(xT)
+    keep.update(xT=xT, ck=ck, loss=loss, dmu=dmu, dsig=dsig, dx0=dx0)
+
+    def run3(sh):
+        orand.orand_walk3d_fwd(ctx, prm3, 0, xT.data_ptr(), ck.data_ptr(), loss.data_ptr(), sh)
+        orand.orand_walk3d_bwd(ctx, prm3, xT.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(), dx0.data_ptr(), sh)
+
+    rows.append(Row("walk3d/fused_fwd+adjoint", run3, P3 * T, "particle-steps", 5))
+    return rows, keep
+
+
+def plain_walk3d_baseline(torch, orand, W, reps=2, chunk=1 << 20):
+    """The plain noise-storing walk (one launch per step, z stored in forward
+    and read back in backward), run over particle chunks so that the stored
+    noise of one chunk (steps x chunk x 3 floats = 48 GiB) fits in HBM."""
+    c3 = W.WALK3D
+    P3, T = c3["n_particles"], c3["steps"]
+    ctx = orand.default_context().handle
+    sh = torch.cuda.current_stream().cuda_stream
+    z = torch.empty((T, chunk, 3), dtype=torch.float32, device="cuda")
+    x = torch.empty((chunk, 3), dtype=torch.float32, device="cuda")
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    dmu = torch.empty(3, dtype=torch.float64, device="cuda")
+    dsig = torch.empty((), dtype=torch.float64, device="cuda")
+    dx0 = torch.empty_like(x)
+    times = []
+    launches = 0
+    for r in range(reps + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for c0 in range(0, P3, chunk):
+            prm = orand.walk3d_params(chunk, T, c3["dt"], c3["mu"], c3["sigma"], c3["k"], c3["seed"], 0,
+                                      p_first=c0, p_total=P3)
+            orand.orand_walk3d_plain_fwd(ctx, prm, 0, x.data_ptr(), z.data_ptr(), loss.data_ptr(), sh)
+            orand.orand_walk3d_plain_bwd(ctx, prm, x.data_ptr(), z.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(),
+                                         dx0.data_ptr(), sh)
+            launches += (1 + T + 2) + (T + 3)
+        b.record()
+        torch.cuda.synchronize()
+        if r:
+            times.append(a.elapsed_time(b))
+    del z
+    torch.cuda.empty_cache()
+    ms = statistics.mean(times)
+    return {"ms": round(ms, 3), "particle_steps_per_s": P3 * T / (ms * 1e-3),
+            "pattern": "one launch per step, noise stored (%d GiB per %d-particle chunk)" % (
+                T * chunk * 12 >> 30, chunk),
+            "launches_per_run": launches // (reps + 1)}
+
+
 # ---------------------------------------------------------------- reference --
 
 def cpu_oracle_fill_rate(threads, n_streams=1 << 21, dps=16):
@@ -221,6 +298,8 @@ def main():
 
     rows, _keep = fill_rows(torch, orand, W, rank)
     head = rows[0]  # fill/philox4x32_10/u32: the headline kernel
+    wrows, _wkeep = walk_rows(torch, orand, W, rank)
+    rows += wrows
     if args.only:
         rows = [r for r in rows if args.only in r.name]
         if head not in rows:
@@ -278,7 +357,7 @@ def main():
     row_table = {}
     for r in rows:
         t = max_over_ranks(statistics.mean(r.times_ms))
-        e = {"ms": round(t, 4), "unit_per_s": world * r.units / (t * 1e-3)}
+        e = {"ms": round(t, 4), r.unit + "_per_s": world * r.units / (t * 1e-3)}
         if r.bytes_written:
             e["GB/s"] = round(world * r.bytes_written / (t * 1e-3) / 1e9, 1)
             e["frac_hbm"] = round(r.bytes_written / (t * 1e-3) / 1e9 / peak, 4)
@@ -302,6 +381,14 @@ def main():
     e2e_t = max_over_ranks(statistics.mean(e2e_ms))
     e2e = {"value": world * head.bytes_written / (e2e_t * 1e-3) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": head.bytes_written}
+
+    baselines = {}
+    if not args.only and world == 1:
+        fused = row_table.get("walk3d/fused_fwd+adjoint")
+        plain = plain_walk3d_baseline(torch, orand, W)
+        if fused:
+            plain["fused_speedup"] = round(plain["ms"] / fused["ms"], 3)
+        baselines["walk3d/plain_noise_storing_fwd+bwd"] = plain
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -327,6 +414,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": sum(r.kernels for r in rows) * args.steps,
             "rows": row_table,
+            "baselines": baselines,
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

@@ -93,6 +93,166 @@ orand_status_t orand_fill_normal_f32(orand_gen_t gen, uint64_t seed, uint32_t co
 orand_status_t orand_fill(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, uint32_t counter,
                           uint64_t n_streams, uint64_t draws_per_stream, void *out, cudaStream_t stream);
 
+
+/* ------------------------------------------------------------------------
+ * Context: owns the library's device scratch (reduction partials, ragged
+ * work tables, per-particle accumulators of the baseline walk), the ragged
+ * batcher's tuning table and its CUDA-graph cache.  A context belongs to the
+ * device that was current at creation; use it from one host thread at a
+ * time.  orand_ctx_destroy synchronises that device before freeing.
+ * Errors: ORAND_ERR_INVALID_ARG (NULL), ORAND_ERR_ALLOC, ORAND_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct orand_ctx_s *orand_ctx_t;
+orand_status_t orand_ctx_create(orand_ctx_t *ctx);
+orand_status_t orand_ctx_destroy(orand_ctx_t ctx);
+
+/* ------------------------------------------------------------------------
+ * Fused 2D Brownian walk: the paper's macro-benchmark (Fig. 1, §5) in its
+ * pure-diffusion FP32 form, all state in registers, one store per particle.
+ * Particle i (0-based in the call) has global id g = p_first + i and key
+ * seed ^ g.  Its start position is (u(w0), u(w1)) from the Philox block
+ * with counter (0, 0, 0, 0).  Step t = 1..steps adds s * (z0, z1), where
+ * (z0, z1) is Box-Muller of words 0 and 1 of the block with counter
+ * (0, t, 0, 0) and s = sqrt(2 D dt) (rounded once to FP32).  The sum is
+ * compensated (Kahan).  pos_out: 2 * n_particles floats (x, y interleaved),
+ * 8-byte aligned.
+ * Errors: INVALID_ARG (NULL p or pos_out with n > 0, dt or D negative or
+ * not finite), OVERFLOW (p_first + n wraps), ALIGNMENT, CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct orand_walk2d_t {
+    uint64_t n_particles;
+    uint64_t p_first;
+    uint64_t seed;
+    uint32_t steps;
+    float dt;
+    float D;
+    uint32_t reserved;
+} orand_walk2d_t;
+orand_status_t orand_brownian_walk(const orand_walk2d_t *p, float *pos_out, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Differentiable 3D Brownian walk with constant drift.
+ * x_{t+1} = x_t + mu dt + sigma sqrt(dt) z_t, t = 0..steps-1, where z_t are
+ * the first three Box-Muller normals of the Philox block with counter
+ * (0, t+1, 0, 0) and key seed ^ (p_first + i): (z0, z1) from words 0-1,
+ * z2 the cosine normal of words 2-3.  x_0 is given, or else
+ * 2 u(w_c) - 1, c = 0..2, from the block with counter (0, 0, 0, 0).
+ * The loss is L = (1 / p_total) * sum_i 0.5 k |x_T,i|^2, where p_total
+ * is the whole problem's particle count (0 means n_particles).  With this
+ * normaliser, calls over particle ranges add up.
+ * Layouts: x0, xT, dx0 are n_particles x 3 floats (xyz per particle).  ckpt
+ * is ceil(steps / ckpt_every) x n_particles x 3 floats, with checkpoint
+ * j = x_{j * ckpt_every}.  The scalar reductions (loss, dmu[3], dsigma)
+ * are FP64 device values, summed in a fixed order: results are
+ * bit-reproducible.
+ * ---------------------------------------------------------------------- */
+typedef struct orand_walk3d_t {
+    uint64_t n_particles;
+    uint64_t p_first;
+    uint64_t p_total;
+    uint64_t seed;
+    uint32_t steps;
+    uint32_t ckpt_every;  /* checkpoint interval K in steps; 0 = none */
+    float dt;
+    float mu[3];
+    float sigma;
+    float k;
+} orand_walk3d_t;
+
+/* x0 = 2u - 1 from counter 0, as the forward uses when x0 is NULL. */
+orand_status_t orand_walk3d_init(const orand_walk3d_t *p, float *x0, cudaStream_t stream);
+
+/* Forward: writes xT, the checkpoints (if ckpt is not NULL and ckpt_every > 0)
+ * and the loss (if loss is not NULL).  Uses ctx scratch for the loss
+ * reduction. */
+orand_status_t orand_walk3d_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *xT,
+                                float *ckpt, double *loss, cudaStream_t stream);
+
+/* Adjoint: regenerates every z_t from its (particle, t+1) key instead of
+ * reading stored noise.  Writes dL/dmu (3 doubles), dL/dsigma (1 double)
+ * and dL/dx0 (n x 3 floats, may be NULL), each scaled by *grad_loss
+ * (a device double; NULL means 1).  The drift does not depend on x, so
+ * dx_{t+1}/dx_t = I and the adjoint needs only x_T, not the checkpoints. */
+orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
+                                const double *grad_loss, double *dmu, double *dsigma, float *dx0,
+                                cudaStream_t stream);
+
+/* Plain baseline of the same walk, in the paper's one-launch-per-step
+ * pattern (Fig. 1 host loop).  It stores every noise draw: z_store is
+ * steps x n_particles x 3 floats.  It works on x in place, starting from
+ * x0 (or the counter-0 init), and accumulates without compensation.  The
+ * backward reads z_store back, one launch per step, and keeps its
+ * per-particle accumulators in ctx scratch.  The outputs are those of
+ * orand_walk3d_fwd / orand_walk3d_bwd, up to FP32 summation order. */
+orand_status_t orand_walk3d_plain_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *x,
+                                      float *z_store, double *loss, cudaStream_t stream);
+orand_status_t orand_walk3d_plain_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
+                                      const float *z_store, const double *grad_loss, double *dmu,
+                                      double *dsigma, float *dx0, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Ragged batched generation.  Request i asks for `length` values of
+ * `dtype` from the single stream (gen, key64 = seed, counter): exactly the
+ * values orand_fill would write for n_streams = 1 with that seed.  They go
+ * to (char *)out_base + out_offset_bytes.  reqs is a HOST array; the
+ * library copies it before returning, so the caller may reuse it at once.
+ * One persistent kernel serves the whole batch from a cached CUDA graph
+ * (host-to-device table copy + kernel).  Its block size, chunk size and
+ * store width come from an autotuner: the first call for a new size class
+ * (log2 of total values, log2 of request count, any Tyche) times candidate
+ * configurations on the caller's batch, synchronising the stream.  Every
+ * configuration writes identical bits.  Set ORAND_AUTOTUNE=0 to use the
+ * default configuration, or pin one with orand_ragged_set_config.
+ * Requirements: each output range lies inside [0, out_bytes) and is
+ * aligned to its element size (4 or 8 bytes).  A start on a 16-byte
+ * boundary takes 16-byte stores.  Ranges must not overlap; they are
+ * checked only when ORAND_CHECK_OVERLAP=1.  reserved must be 0.  A stream
+ * needs at most 2^32 generator words.  Calls sharing one ctx are ordered:
+ * each call waits for the previous batch of that ctx, whatever its stream.
+ * Errors: INVALID_ARG, OVERFLOW (range past out_bytes, too many words),
+ * ALIGNMENT, ALLOC, CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct orand_request_t {
+    uint32_t gen;              /* orand_gen_t */
+    uint32_t dtype;            /* orand_dtype_t */
+    uint64_t seed;             /* the stream's 64-bit key */
+    uint32_t counter;          /* the stream's 32-bit counter */
+    uint32_t reserved;         /* must be 0 */
+    uint64_t length;           /* values */
+    uint64_t out_offset_bytes; /* from out_base */
+} orand_request_t;
+
+orand_status_t orand_fill_ragged(orand_ctx_t ctx, const orand_request_t *reqs, size_t n, void *out_base,
+                                 uint64_t out_bytes, cudaStream_t stream);
+
+/* The same batch as one bulk-fill launch per request, in request order, on
+ * one stream: the plain baseline the batcher is measured against. */
+orand_status_t orand_fill_ragged_serial(const orand_request_t *reqs, size_t n, void *out_base,
+                                        uint64_t out_bytes, cudaStream_t stream);
+
+/* Batcher configuration: block in {64,128,256,512,1024}; chunk_values a
+ * multiple of 4 in [128, 2^24]; store_bytes in {4, 8, 16}; ctas_per_sm
+ * 0 (as many as fit) or a cap.  set(NULL) returns to autotuning; get
+ * reports the configuration of the last call. */
+typedef struct orand_ragged_config_t {
+    uint32_t block;
+    uint32_t chunk_values;
+    uint32_t store_bytes;
+    uint32_t ctas_per_sm;
+} orand_ragged_config_t;
+orand_status_t orand_ragged_set_config(orand_ctx_t ctx, const orand_ragged_config_t *cfg);
+orand_status_t orand_ragged_get_config(orand_ctx_t ctx, orand_ragged_config_t *cfg);
+
+/* Counters of the batcher on this ctx: graph launches and (re)builds,
+ * autotuning runs, size classes tuned. */
+typedef struct orand_ragged_stats_t {
+    uint64_t graph_launches;
+    uint64_t graph_builds;
+    uint64_t tune_runs;
+    uint64_t tuned_classes;
+} orand_ragged_stats_t;
+orand_status_t orand_ragged_stats(orand_ctx_t ctx, orand_ragged_stats_t *stats);
+
 #ifdef __cplusplus
 }  /* extern "C" */
 #endif

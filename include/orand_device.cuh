@@ -261,6 +261,14 @@ __device__ __forceinline__ float2 box_muller_f32(uint32_t w0, uint32_t w1)
     return make_float2(r * c, r * s);
 }
 
+/* Cosine half of a Box-Muller pair: r cos(2 pi u2), the first normal. */
+__device__ __forceinline__ float box_muller_cos_f32(uint32_t w0, uint32_t w1)
+{
+    const float u1 = __uint2float_rn((w0 >> 8) + 1u) * 0x1p-24f;
+    const float two_u2 = __uint2float_rn(w1 >> 8) * 0x1p-23f;
+    return sqrtf(-2.0f * logf(u1)) * cospif(two_u2);
+}
+
 /* ------------------------------------------------ engine-style generators */
 
 /* Sequential draw interface of the paper's API (§3): construct from

@@ -53,7 +53,31 @@ _SIGS = {
     "orand_fill_uniform_f32": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
     "orand_fill_uniform_f64": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
     "orand_fill_normal_f32": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
+    "orand_ctx_create": (_i32, [ctypes.POINTER(_vp)]),
+    "orand_ctx_destroy": (_i32, [_vp]),
+    "orand_brownian_walk": (_i32, [_vp, _vp, _vp]),
+    "orand_walk3d_init": (_i32, [_vp, _vp, _vp]),
+    "orand_walk3d_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_walk3d_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_walk3d_plain_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_walk3d_plain_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
+
+
+class Walk2DParams(ctypes.Structure):
+    """orand_walk2d_t."""
+    _fields_ = [("n_particles", _u64), ("p_first", _u64), ("seed", _u64), ("steps", _u32),
+                ("dt", _f32), ("D", _f32), ("reserved", _u32)]
+
+
+class Walk3DParams(ctypes.Structure):
+    """orand_walk3d_t."""
+    _fields_ = [("n_particles", _u64), ("p_first", _u64), ("p_total", _u64), ("seed", _u64),
+                ("steps", _u32), ("ckpt_every", _u32), ("dt", _f32), ("mu", _f32 * 3), ("sigma", _f32),
+                ("k", _f32)]
+
+
+assert ctypes.sizeof(Walk2DParams) == 40 and ctypes.sizeof(Walk3DParams) == 64
 
 
 def _lib():
@@ -90,6 +114,34 @@ def _ptr(t) -> int:
 
 
 # ---------------------------------------------------------------- raw C ABI --
+
+class Context:
+    """An orand_ctx_t: device scratch, ragged tuning table and graph cache."""
+
+    def __init__(self):
+        h = _vp()
+        _check(_lib().orand_ctx_create(ctypes.byref(h)), "orand_ctx_create")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            _check(_lib().orand_ctx_destroy(self.handle), "orand_ctx_destroy")
+            self.handle = None
+
+
+_CONTEXTS = {}
+
+
+def default_context(device=None) -> Context:
+    """One library context per device, created on first use and kept for the process."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _CONTEXTS:
+        with torch.cuda.device(dev):
+            _CONTEXTS[dev] = Context()
+    return _CONTEXTS[dev]
+
 
 def orand_fill(gen, dtype, seed, counter, n_streams, draws_per_stream, out_ptr, stream_handle):
     _check(_lib().orand_fill(gen, dtype, seed & (2**64 - 1), counter & 0xFFFFFFFF, n_streams,
@@ -139,3 +191,147 @@ def fill(gen: int, dtype: int, seed: int, counter: int, n_streams: int, draws_pe
     orand_fill(gen, dtype, seed, counter, n_streams, draws_per_stream, _ptr(out) if n else 0,
                _stream_handle(stream))
     return out
+
+
+# ------------------------------------------------------------------ walks --
+
+def walk2d_params(n_particles, steps, dt=1e-3, D=1.0, seed=0, p_first=0) -> Walk2DParams:
+    return Walk2DParams(n_particles, p_first, seed & (2**64 - 1), steps, dt, D, 0)
+
+
+def orand_brownian_walk(params: Walk2DParams, pos_out_ptr, stream_handle):
+    _check(_lib().orand_brownian_walk(ctypes.byref(params), pos_out_ptr, stream_handle), "orand_brownian_walk")
+
+
+def brownian_walk(n_particles, steps, dt=1e-3, D=1.0, seed=0, p_first=0, out=None, stream=None):
+    """Fused 2D walk; returns an (n_particles, 2) float32 CUDA tensor of final positions."""
+    import torch
+
+    if out is None:
+        out = torch.empty((n_particles, 2), dtype=torch.float32, device="cuda")
+    orand_brownian_walk(walk2d_params(n_particles, steps, dt, D, seed, p_first), _ptr(out) if n_particles else 0,
+                        _stream_handle(stream))
+    return out
+
+
+def walk3d_params(n_particles, steps, dt=1e-3, mu=(0.1, -0.2, 0.05), sigma=0.5, k=2.0, seed=0,
+                  ckpt_every=64, p_first=0, p_total=0) -> Walk3DParams:
+    return Walk3DParams(n_particles, p_first, p_total, seed & (2**64 - 1), steps, ckpt_every, dt,
+                        (_f32 * 3)(*[float(m) for m in mu]), float(sigma), float(k))
+
+
+def n_checkpoints(steps, ckpt_every):
+    return 0 if not ckpt_every else (steps + ckpt_every - 1) // ckpt_every
+
+
+def orand_walk3d_init(params, x0_ptr, stream_handle):
+    _check(_lib().orand_walk3d_init(ctypes.byref(params), x0_ptr, stream_handle), "orand_walk3d_init")
+
+
+def orand_walk3d_fwd(ctx, params, x0_ptr, xT_ptr, ckpt_ptr, loss_ptr, stream_handle):
+    _check(_lib().orand_walk3d_fwd(ctx, ctypes.byref(params), x0_ptr, xT_ptr, ckpt_ptr, loss_ptr,
+                                   stream_handle), "orand_walk3d_fwd")
+
+
+def orand_walk3d_bwd(ctx, params, xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dx0_ptr, stream_handle):
+    _check(_lib().orand_walk3d_bwd(ctx, ctypes.byref(params), xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr,
+                                   dx0_ptr, stream_handle), "orand_walk3d_bwd")
+
+
+def orand_walk3d_plain_fwd(ctx, params, x0_ptr, x_ptr, z_ptr, loss_ptr, stream_handle):
+    _check(_lib().orand_walk3d_plain_fwd(ctx, ctypes.byref(params), x0_ptr, x_ptr, z_ptr, loss_ptr,
+                                         stream_handle), "orand_walk3d_plain_fwd")
+
+
+def orand_walk3d_plain_bwd(ctx, params, xT_ptr, z_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dx0_ptr,
+                           stream_handle):
+    _check(_lib().orand_walk3d_plain_bwd(ctx, ctypes.byref(params), xT_ptr, z_ptr, grad_loss_ptr, dmu_ptr,
+                                         dsigma_ptr, dx0_ptr, stream_handle), "orand_walk3d_plain_bwd")
+
+
+def walk3d_init(params: Walk3DParams, stream=None):
+    """x0 = 2u - 1 from counter 0 for every particle: (n, 3) float32."""
+    import torch
+
+    x0 = torch.empty((params.n_particles, 3), dtype=torch.float32, device="cuda")
+    orand_walk3d_init(params, _ptr(x0), _stream_handle(stream))
+    return x0
+
+
+def walk3d_forward(params: Walk3DParams, x0=None, want_ckpt=True, stream=None):
+    """Fused forward: returns (xT (n,3) f32, ckpt (C,n,3) f32 or None, loss 0-dim f64)."""
+    import torch
+
+    n = params.n_particles
+    xT = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    C = n_checkpoints(params.steps, params.ckpt_every) if want_ckpt else 0
+    ckpt = torch.empty((C, n, 3), dtype=torch.float32, device="cuda") if C else None
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    if x0 is not None:
+        x0 = x0.detach().contiguous()
+    orand_walk3d_fwd(default_context().handle, params, _ptr(x0), _ptr(xT), _ptr(ckpt), _ptr(loss),
+                     _stream_handle(stream))
+    return xT, ckpt, loss
+
+
+def walk3d_backward(params: Walk3DParams, xT, grad_loss=None, stream=None):
+    """Noise-regenerating adjoint: returns (dmu (3,) f64, dsigma 0-dim f64, dx0 (n,3) f32)."""
+    import torch
+
+    dmu = torch.empty(3, dtype=torch.float64, device="cuda")
+    dsig = torch.empty((), dtype=torch.float64, device="cuda")
+    dx0 = torch.empty_like(xT)
+    g = None if grad_loss is None else grad_loss.detach().to(device="cuda", dtype=torch.float64).contiguous()
+    orand_walk3d_bwd(default_context().handle, params, _ptr(xT.contiguous()), _ptr(g), _ptr(dmu), _ptr(dsig),
+                     _ptr(dx0), _stream_handle(stream))
+    return dmu, dsig, dx0
+
+
+def _autograd_function():
+    import torch
+
+    class BrownianWalk3D(torch.autograd.Function):
+        """loss = BrownianWalk3D.apply(mu, sigma, x0, steps, dt, k, seed, ckpt_every)
+
+        Forward runs the fused walk (checkpoints every `ckpt_every` steps are
+        kept on the context for inspection via `last_checkpoints`); backward
+        runs the adjoint kernel, which regenerates every noise draw from its
+        (particle, step) key instead of storing it.  mu: (3,) tensor,
+        sigma: 0-dim tensor (either may require grad), x0: (n, 3) CUDA float32.
+        """
+
+        last_checkpoints = None
+
+        @staticmethod
+        def forward(ctx, mu, sigma, x0, steps, dt=1e-3, k=2.0, seed=0, ckpt_every=64):
+            mu_v = [float(v) for v in mu.detach().cpu().tolist()]
+            p = walk3d_params(x0.shape[0], int(steps), float(dt), mu_v, float(sigma.detach().cpu()), float(k),
+                              int(seed), int(ckpt_every))
+            xT, ckpt, loss = walk3d_forward(p, x0=x0, want_ckpt=bool(ckpt_every))
+            BrownianWalk3D.last_checkpoints = ckpt
+            ctx.params = p
+            ctx.mu_meta = (mu.dtype, mu.device)
+            ctx.sigma_meta = (sigma.dtype, sigma.device)
+            ctx.save_for_backward(xT)
+            return loss
+
+        @staticmethod
+        def backward(ctx, grad_loss):
+            (xT,) = ctx.saved_tensors
+            dmu, dsig, dx0 = walk3d_backward(ctx.params, xT, grad_loss)
+            return (dmu.to(dtype=ctx.mu_meta[0], device=ctx.mu_meta[1]),
+                    dsig.to(dtype=ctx.sigma_meta[0], device=ctx.sigma_meta[1]), dx0,
+                    None, None, None, None, None)
+
+    return BrownianWalk3D
+
+
+_BW3D = None
+
+
+def BrownianWalk3D():
+    """The torch.autograd.Function class for the differentiable 3D walk."""
+    global _BW3D
+    if _BW3D is None:
+        _BW3D = _autograd_function()
+    return _BW3D

@@ -2,8 +2,10 @@
 // error, cached device properties.
 #include <atomic>
 #include <mutex>
+#include <new>
 
 #include "common.cuh"
+#include "ctx.cuh"
 
 namespace orand_impl {
 
@@ -53,9 +55,73 @@ orand_status_t current_device(DeviceInfo *info)
     return c.status[dev];
 }
 
+orand_status_t ctx_check(orand_ctx_t ctx)
+{
+    if (ctx == nullptr) return ORAND_ERR_INVALID_ARG;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    return dev == ctx->device ? ORAND_OK : ORAND_ERR_INVALID_ARG;
+}
+
+orand_status_t ctx_scratch(orand_ctx_t ctx, size_t bytes, void **ptr)
+{
+    orand_status_t st = ctx_check(ctx);
+    if (st != ORAND_OK) return st;
+    if (bytes > ctx->scratch_bytes) {
+        const size_t want = (bytes + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+        if (ctx->scratch) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_status(e);
+            cudaFree(ctx->scratch);
+            ctx->scratch = nullptr;
+            ctx->scratch_bytes = 0;
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            set_last_cuda_error(cudaGetLastError());
+            return ORAND_ERR_ALLOC;
+        }
+        ctx->scratch = p;
+        ctx->scratch_bytes = want;
+    }
+    *ptr = ctx->scratch;
+    return ORAND_OK;
+}
+
+void ragged_state_free(orand_ctx_t ctx);
+
 }  // namespace orand_impl
 
 extern "C" {
+
+orand_status_t orand_ctx_create(orand_ctx_t *ctx)
+{
+    if (ctx == nullptr) return ORAND_ERR_INVALID_ARG;
+    *ctx = nullptr;
+    orand_impl::DeviceInfo info;
+    orand_status_t st = orand_impl::current_device(&info);
+    if (st != ORAND_OK) return st;
+    orand_ctx_s *c = new (std::nothrow) orand_ctx_s();
+    if (c == nullptr) return ORAND_ERR_ALLOC;
+    c->device = info.device;
+    *ctx = c;
+    return ORAND_OK;
+}
+
+orand_status_t orand_ctx_destroy(orand_ctx_t ctx)
+{
+    if (ctx == nullptr) return ORAND_ERR_INVALID_ARG;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    orand_impl::ragged_state_free(ctx);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete ctx;
+    return orand_impl::cuda_status(e);
+}
 
 const char *orand_status_string(orand_status_t status)
 {

@@ -11,6 +11,7 @@
 // resident capacity of the 148 SMs and strides over the groups.
 #include "common.cuh"
 #include "orand_device.cuh"
+#include "values.cuh"
 
 namespace orand_impl {
 
@@ -25,78 +26,6 @@ struct FillArgs {
     uint32_t counter;
     void *out;
 };
-
-// Four words 4b..4b+3 of the stream (key64, counter) for the random-access
-// generators.
-template <int GEN>
-__device__ __forceinline__ uint4 group_words(uint64_t key64, uint32_t counter, uint32_t b)
-{
-    if (GEN == ORAND_PHILOX4x32_10) return orand::philox_block(key64, counter, b);
-    if (GEN == ORAND_THREEFRY4x32_20) return orand::threefry_block(key64, counter, b);
-    return orand::squares_block(orand::squares_key(key64), counter, b);
-}
-
-// Values per group for a dtype.
-template <int DT>
-struct Vals {
-    static constexpr uint32_t V = (DT == ORAND_F64_UNIFORM) ? 2u : 4u;
-};
-
-// Write the values of group b of stream s.  VEC: one 16-byte store at the
-// group's contiguous slot g.  Otherwise: element stores masked to j < dps.
-template <int DT, bool VEC>
-__device__ __forceinline__ void store_group(void *out, uint64_t g, uint64_t s, uint32_t b, uint64_t dps,
-                                            uint4 w)
-{
-    if (DT == ORAND_U32) {
-        uint32_t *o = (uint32_t *)out;
-        if (VEC) {
-            reinterpret_cast<uint4 *>(o)[g] = w;
-        } else {
-            const uint64_t j0 = (uint64_t)b * 4u, base = s * dps + j0;
-            const uint32_t v[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (j0 + i < dps) o[base + i] = v[i];
-        }
-    } else if (DT == ORAND_F32_UNIFORM) {
-        float4 f = make_float4(orand::u01_f32(w.x), orand::u01_f32(w.y), orand::u01_f32(w.z),
-                               orand::u01_f32(w.w));
-        float *o = (float *)out;
-        if (VEC) {
-            reinterpret_cast<float4 *>(o)[g] = f;
-        } else {
-            const uint64_t j0 = (uint64_t)b * 4u, base = s * dps + j0;
-            const float v[4] = {f.x, f.y, f.z, f.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (j0 + i < dps) o[base + i] = v[i];
-        }
-    } else if (DT == ORAND_F64_UNIFORM) {
-        double2 d = make_double2(orand::u01_f64(w.x, w.y), orand::u01_f64(w.z, w.w));
-        double *o = (double *)out;
-        if (VEC) {
-            reinterpret_cast<double2 *>(o)[g] = d;
-        } else {
-            const uint64_t j0 = (uint64_t)b * 2u, base = s * dps + j0;
-            if (j0 < dps) o[base] = d.x;
-            if (j0 + 1 < dps) o[base + 1] = d.y;
-        }
-    } else {
-        const float2 p = orand::box_muller_f32(w.x, w.y);
-        const float2 q = orand::box_muller_f32(w.z, w.w);
-        float *o = (float *)out;
-        if (VEC) {
-            reinterpret_cast<float4 *>(o)[g] = make_float4(p.x, p.y, q.x, q.y);
-        } else {
-            const uint64_t j0 = (uint64_t)b * 4u, base = s * dps + j0;
-            const float v[4] = {p.x, p.y, q.x, q.y};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (j0 + i < dps) o[base + i] = v[i];
-        }
-    }
-}
 
 // Random-access generators: grid-stride over groups; (s, b) advance
 // incrementally so the loop needs no 64-bit division.

@@ -1,0 +1,644 @@
+// Ragged batched generation: many independent requests (generator, dtype,
+// seed, counter, length, output offset) served by one persistent kernel
+// launched from a cached CUDA graph.  A request is exactly the single-stream
+// bulk fill (stream 0, key = its seed), so the two paths emit identical bits.
+//
+// Scheduling (host, O(n log n)):
+//   * Tyche is sequential within a stream, so each Tyche request is one
+//     lane's serial chain.  Requests are sorted longest first (LPT) and taken
+//     32 at a time by warps, so the longest chains start first and warps see
+//     similar lengths.
+//   * The random-access generators (Philox, Threefry, Squares) are cut into
+//     chunks of `chunk_values` values.  A warp takes one chunk at a time; its
+//     32 lanes write consecutive 16-byte groups, and per-stream setup (round
+//     keys, Squares key hash) is paid once per chunk.
+// Warps claim work through two atomic cursors (Tyche items first, then
+// chunks).  There are no inter-block waits.
+//
+// Autotuning: block size, chunk size and store width (16/8/4-byte stores)
+// are timed on the caller's batch the first time a size class is seen.  The
+// output is written again each time with the same bits.  The fastest
+// configuration is kept per size class in the context.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.cuh"
+#include "values.cuh"
+
+namespace orand_impl {
+
+struct RaggedReq {
+    uint64_t seed;
+    uint64_t length;      // values
+    uint64_t out_off;     // bytes from out_base
+    uint64_t first_item;  // first chunk item (random-access requests)
+    uint32_t counter;
+    uint8_t gen, dtype, vec, pad;
+};
+static_assert(sizeof(RaggedReq) == 40, "RaggedReq layout");
+
+struct RaggedArgs {
+    const RaggedReq *reqs;
+    const uint32_t *item_req;     // request index of each chunk item
+    const uint32_t *tyche_order;  // Tyche request indices, longest first
+    unsigned long long *cursors;  // [0] Tyche warp items, [1] chunk items
+    uint64_t n_items;
+    uint64_t chunk_values;
+    uint32_t n_ty;
+    uint32_t n_ty_items;
+    char *out;
+};
+
+// 16-byte store of one group's bits as SW-byte stores (dst 16-byte aligned).
+template <int SW>
+__device__ __forceinline__ void store16(char *dst, uint4 v)
+{
+    if (SW == 16) {
+        *reinterpret_cast<uint4 *>(dst) = v;
+    } else if (SW == 8) {
+        reinterpret_cast<uint2 *>(dst)[0] = make_uint2(v.x, v.y);
+        reinterpret_cast<uint2 *>(dst)[1] = make_uint2(v.z, v.w);
+    } else {
+        uint32_t *o = reinterpret_cast<uint32_t *>(dst);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+}
+
+// Store group g of a request with L values at base.
+template <int DT, int SW>
+__device__ __forceinline__ void store_req_group(char *base, bool vec, uint64_t g, uint64_t L, uint4 w)
+{
+    constexpr uint32_t V = Vals<DT>::V;
+    constexpr uint32_t E = DT == ORAND_F64_UNIFORM ? 8u : 4u;
+    const uint4 v = group_bits<DT>(w);
+    const uint64_t j0 = g * V;
+    if (vec && j0 + V <= L) store16<SW>(base + j0 * E, v);
+    else store_bits_masked<DT>(base + j0 * E, j0, L, v);
+}
+
+template <int SW>
+__device__ __forceinline__ void store_req_group_rt(int dt, char *base, bool vec, uint64_t g, uint64_t L, uint4 w)
+{
+    switch (dt) {
+    case ORAND_U32: store_req_group<ORAND_U32, SW>(base, vec, g, L, w); break;
+    case ORAND_F32_UNIFORM: store_req_group<ORAND_F32_UNIFORM, SW>(base, vec, g, L, w); break;
+    case ORAND_F64_UNIFORM: store_req_group<ORAND_F64_UNIFORM, SW>(base, vec, g, L, w); break;
+    default: store_req_group<ORAND_F32_NORMAL, SW>(base, vec, g, L, w); break;
+    }
+}
+
+// One lane serves one whole Tyche request.
+template <int SW>
+__device__ __forceinline__ void tyche_request(const RaggedReq &q, char *out)
+{
+    char *base = out + q.out_off;
+    const uint64_t V = q.dtype == ORAND_F64_UNIFORM ? 2u : 4u;
+    const uint64_t G = (q.length + V - 1) / V;
+    orand::TycheState st = orand::tyche_init(q.seed, q.counter);
+    for (uint64_t g = 0; g < G; ++g) {
+        uint4 w;
+        w.x = orand::tyche_next(st);
+        w.y = orand::tyche_next(st);
+        w.z = orand::tyche_next(st);
+        w.w = orand::tyche_next(st);
+        store_req_group_rt<SW>(q.dtype, base, q.vec, g, q.length, w);
+    }
+}
+
+// A warp serves groups [g0, g1) of one random-access request.
+template <int GEN, int DT, int SW>
+__device__ __forceinline__ void chunk_groups(const RaggedReq &q, char *out, uint64_t g0, uint64_t g1, int lane)
+{
+    char *base = out + q.out_off;
+    if (GEN == ORAND_PHILOX4x32_10) {
+        const orand::PhiloxKeys keys(q.seed);
+        for (uint64_t g = g0 + lane; g < g1; g += 32)
+            store_req_group<DT, SW>(base, q.vec, g, q.length, keys.block((uint32_t)g, q.counter));
+    } else if (GEN == ORAND_THREEFRY4x32_20) {
+        const uint4 key = make_uint4((uint32_t)q.seed, (uint32_t)(q.seed >> 32), 0u, 0u);
+        for (uint64_t g = g0 + lane; g < g1; g += 32)
+            store_req_group<DT, SW>(base, q.vec, g, q.length,
+                                    orand::threefry4x32_20(make_uint4((uint32_t)g, q.counter, 0u, 0u), key));
+    } else {
+        const uint64_t sk = orand::squares_key(q.seed);
+        for (uint64_t g = g0 + lane; g < g1; g += 32)
+            store_req_group<DT, SW>(base, q.vec, g, q.length, orand::squares_block(sk, q.counter, (uint32_t)g));
+    }
+}
+
+template <int GEN, int SW>
+__device__ __forceinline__ void chunk_dt(const RaggedReq &q, char *out, uint64_t g0, uint64_t g1, int lane)
+{
+    switch (q.dtype) {
+    case ORAND_U32: chunk_groups<GEN, ORAND_U32, SW>(q, out, g0, g1, lane); break;
+    case ORAND_F32_UNIFORM: chunk_groups<GEN, ORAND_F32_UNIFORM, SW>(q, out, g0, g1, lane); break;
+    case ORAND_F64_UNIFORM: chunk_groups<GEN, ORAND_F64_UNIFORM, SW>(q, out, g0, g1, lane); break;
+    default: chunk_groups<GEN, ORAND_F32_NORMAL, SW>(q, out, g0, g1, lane); break;
+    }
+}
+
+template <int SW>
+__global__ void ragged_kernel(RaggedArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    // Phase 1: Tyche requests, 32 per warp item, longest first.
+    for (;;) {
+        unsigned long long wi = 0;
+        if (lane == 0) wi = atomicAdd(&a.cursors[0], 1ull);
+        wi = __shfl_sync(0xFFFFFFFFu, wi, 0);
+        if (wi >= a.n_ty_items) break;
+        const uint64_t k = wi * 32 + lane;
+        if (k < a.n_ty) {
+            const RaggedReq q = a.reqs[a.tyche_order[k]];
+            tyche_request<SW>(q, a.out);
+        }
+    }
+    // Phase 2: chunks of the random-access requests.
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(&a.cursors[1], 1ull);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= a.n_items) break;
+        const RaggedReq q = a.reqs[a.item_req[item]];
+        const uint64_t V = q.dtype == ORAND_F64_UNIFORM ? 2u : 4u;
+        const uint64_t v0 = (item - q.first_item) * a.chunk_values;
+        const uint64_t v1 = min(q.length, v0 + a.chunk_values);
+        const uint64_t g0 = v0 / V, g1 = (v1 + V - 1) / V;
+        switch (q.gen) {
+        case ORAND_PHILOX4x32_10: chunk_dt<ORAND_PHILOX4x32_10, SW>(q, a.out, g0, g1, lane); break;
+        case ORAND_THREEFRY4x32_20: chunk_dt<ORAND_THREEFRY4x32_20, SW>(q, a.out, g0, g1, lane); break;
+        default: chunk_dt<ORAND_SQUARES32, SW>(q, a.out, g0, g1, lane); break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+struct RaggedConfig {
+    uint32_t block = 256;
+    uint32_t chunk_values = 8192;
+    uint32_t store_bytes = 16;
+    uint32_t ctas_per_sm = 0;  // 0: as many as fit
+};
+
+struct GraphKey {
+    RaggedConfig cfg;
+    uint64_t n_items, table_bytes;
+    uint32_t n_ty, n;
+    char *out;
+    cudaStream_t unused;
+    bool operator==(const GraphKey &o) const
+    {
+        return cfg.block == o.cfg.block && cfg.chunk_values == o.cfg.chunk_values &&
+               cfg.store_bytes == o.cfg.store_bytes && cfg.ctas_per_sm == o.cfg.ctas_per_sm &&
+               n_items == o.n_items && table_bytes == o.table_bytes && n_ty == o.n_ty && n == o.n && out == o.out;
+    }
+};
+
+struct RaggedState {
+    void *d_tables = nullptr;
+    size_t d_bytes = 0;
+    void *h_staging = nullptr;
+    size_t h_bytes = 0;
+    cudaEvent_t staging_free = nullptr;  // recorded in the graph after the table copy
+    cudaEvent_t batch_done = nullptr;    // recorded on the caller's stream after each batch
+    bool batch_pending = false;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GraphKey key{};
+    bool have_graph = false;
+    bool forced = false;
+    RaggedConfig forced_cfg, last_cfg;
+    std::map<std::tuple<int, int, int>, RaggedConfig> tuned;
+    uint64_t graph_launches = 0, graph_builds = 0, tune_runs = 0;
+};
+
+static RaggedState *state_of(orand_ctx_t ctx)
+{
+    if (!ctx->ragged) ctx->ragged = new (std::nothrow) RaggedState();
+    return (RaggedState *)ctx->ragged;
+}
+
+void ragged_state_free(orand_ctx_t ctx)
+{
+    RaggedState *s = (RaggedState *)ctx->ragged;
+    if (!s) return;
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
+    if (s->staging_free) cudaEventDestroy(s->staging_free);
+    if (s->batch_done) cudaEventDestroy(s->batch_done);
+    if (s->d_tables) cudaFree(s->d_tables);
+    if (s->h_staging) cudaFreeHost(s->h_staging);
+    delete s;
+    ctx->ragged = nullptr;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Plan {
+    uint64_t chunk_values = 0;
+    std::vector<RaggedReq> reqs;
+    std::vector<uint32_t> tyche;
+    uint64_t n_items = 0;
+    uint64_t total_values = 0;
+    size_t off_items = 0, off_tyche = 0, off_cursors = 0, table_bytes = 0;
+};
+
+static uint64_t words_for(uint32_t dt, uint64_t len)
+{
+    if (dt == ORAND_F64_UNIFORM) return len > UINT64_MAX / 2 ? UINT64_MAX : 2 * len;
+    if (dt == ORAND_F32_NORMAL) return len + (len & 1);
+    return len;
+}
+
+// Validate every request and build the device tables' host image.
+static orand_status_t plan_requests(const orand_request_t *r, size_t n, const char *out_base, uint64_t out_bytes,
+                                    uint64_t chunk_values, Plan *p, bool check_overlap)
+{
+    p->chunk_values = chunk_values;
+    p->reqs.resize(n);
+    p->tyche.clear();
+    p->n_items = 0;
+    p->total_values = 0;
+    std::vector<std::pair<uint64_t, uint64_t>> ranges;
+    if (check_overlap) ranges.reserve(n);
+    for (size_t i = 0; i < n; ++i) {
+        const orand_request_t &q = r[i];
+        if (q.gen > 3 || q.dtype > 3 || q.reserved != 0) return ORAND_ERR_INVALID_ARG;
+        if (words_for(q.dtype, q.length) > (1ull << 32)) return ORAND_ERR_OVERFLOW;
+        const uint64_t elem = q.dtype == ORAND_F64_UNIFORM ? 8 : 4;
+        const uint64_t bytes = q.length * elem;  // length <= 2^32, no overflow
+        if (q.out_offset_bytes > out_bytes || bytes > out_bytes - q.out_offset_bytes) return ORAND_ERR_OVERFLOW;
+        if (((uintptr_t)out_base + q.out_offset_bytes) % elem) return ORAND_ERR_ALIGNMENT;
+        RaggedReq &d = p->reqs[i];
+        d.seed = q.seed;
+        d.length = q.length;
+        d.out_off = q.out_offset_bytes;
+        d.counter = q.counter;
+        d.gen = (uint8_t)q.gen;
+        d.dtype = (uint8_t)q.dtype;
+        d.vec = (((uintptr_t)out_base + q.out_offset_bytes) % 16 == 0) ? 1 : 0;
+        d.pad = 0;
+        d.first_item = p->n_items;
+        if (q.length && check_overlap) ranges.emplace_back(q.out_offset_bytes, q.out_offset_bytes + bytes);
+        p->total_values += q.length;
+        if (q.length == 0) continue;
+        if (q.gen == ORAND_TYCHE) {
+            if (p->tyche.size() >= 0xFFFFFFFFull) return ORAND_ERR_OVERFLOW;
+            p->tyche.push_back((uint32_t)i);
+        } else {
+            p->n_items += (q.length + chunk_values - 1) / chunk_values;
+        }
+    }
+    if (n > 0xFFFFFFFFull) return ORAND_ERR_OVERFLOW;
+    if (check_overlap) {
+        std::sort(ranges.begin(), ranges.end());
+        for (size_t i = 1; i < ranges.size(); ++i)
+            if (ranges[i].first < ranges[i - 1].second) return ORAND_ERR_INVALID_ARG;
+    }
+    // Longest Tyche chains first; ties by request index keep the plan deterministic.
+    std::sort(p->tyche.begin(), p->tyche.end(), [&](uint32_t a, uint32_t b) {
+        if (p->reqs[a].length != p->reqs[b].length) return p->reqs[a].length > p->reqs[b].length;
+        return a < b;
+    });
+    p->off_items = align_up(n * sizeof(RaggedReq), 256);
+    p->off_tyche = align_up(p->off_items + p->n_items * sizeof(uint32_t), 256);
+    p->off_cursors = align_up(p->off_tyche + p->tyche.size() * sizeof(uint32_t), 256);
+    p->table_bytes = p->off_cursors + 256;
+    return ORAND_OK;
+}
+
+static void write_staging(const Plan &p, char *h)
+{
+    std::memcpy(h, p.reqs.data(), p.reqs.size() * sizeof(RaggedReq));
+    uint32_t *items = (uint32_t *)(h + p.off_items);
+    uint64_t k = 0;
+    for (size_t i = 0; i < p.reqs.size(); ++i) {
+        const RaggedReq &q = p.reqs[i];
+        if (q.gen == ORAND_TYCHE || q.length == 0) continue;
+        const uint64_t n_chunks = (q.length + p.chunk_values - 1) / p.chunk_values;
+        for (uint64_t c = 0; c < n_chunks; ++c) items[k++] = (uint32_t)i;
+    }
+    std::memcpy(h + p.off_tyche, p.tyche.data(), p.tyche.size() * sizeof(uint32_t));
+    std::memset(h + p.off_cursors, 0, 256);
+}
+
+static orand_status_t ensure_buffers(RaggedState *s, size_t bytes)
+{
+    if (!s->staging_free) {
+        if (cudaEventCreateWithFlags(&s->staging_free, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->batch_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_status(cudaGetLastError());
+    }
+    if (bytes > s->d_bytes) {
+        if (s->d_tables) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_status(e);
+            cudaFree(s->d_tables);
+            s->d_tables = nullptr;
+            s->d_bytes = 0;
+        }
+        const size_t want = align_up(bytes + bytes / 4, (size_t)1 << 20);
+        if (cudaMalloc(&s->d_tables, want) != cudaSuccess) {
+            set_last_cuda_error(cudaGetLastError());
+            return ORAND_ERR_ALLOC;
+        }
+        s->d_bytes = want;
+        s->have_graph = false;
+    }
+    if (bytes > s->h_bytes) {
+        if (s->h_staging) {
+            cudaEventSynchronize(s->staging_free);
+            cudaFreeHost(s->h_staging);
+            s->h_staging = nullptr;
+            s->h_bytes = 0;
+        }
+        const size_t want = align_up(bytes + bytes / 4, (size_t)1 << 20);
+        if (cudaHostAlloc(&s->h_staging, want, cudaHostAllocDefault) != cudaSuccess) {
+            set_last_cuda_error(cudaGetLastError());
+            return ORAND_ERR_ALLOC;
+        }
+        s->h_bytes = want;
+        s->have_graph = false;
+    }
+    return ORAND_OK;
+}
+
+static RaggedArgs make_args(const RaggedState *s, const Plan &p, const RaggedConfig &c, char *out)
+{
+    RaggedArgs a;
+    char *d = (char *)s->d_tables;
+    a.reqs = (const RaggedReq *)d;
+    a.item_req = (const uint32_t *)(d + p.off_items);
+    a.tyche_order = (const uint32_t *)(d + p.off_tyche);
+    a.cursors = (unsigned long long *)(d + p.off_cursors);
+    a.n_items = p.n_items;
+    a.chunk_values = c.chunk_values;
+    a.n_ty = (uint32_t)p.tyche.size();
+    a.n_ty_items = (uint32_t)((p.tyche.size() + 31) / 32);
+    a.out = out;
+    return a;
+}
+
+static orand_status_t launch_kernel(const RaggedArgs &a, const RaggedConfig &c, cudaStream_t stream)
+{
+    DeviceInfo info;
+    orand_status_t st = current_device(&info);
+    if (st != ORAND_OK) return st;
+    const void *fn = c.store_bytes == 16 ? (const void *)ragged_kernel<16>
+                     : c.store_bytes == 8 ? (const void *)ragged_kernel<8> : (const void *)ragged_kernel<4>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)c.block, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) per_sm = 1;
+    if (c.ctas_per_sm && (int)c.ctas_per_sm < per_sm) per_sm = (int)c.ctas_per_sm;
+    const unsigned grid = (unsigned)(per_sm * info.sm_count);
+    if (c.store_bytes == 16) ragged_kernel<16><<<grid, c.block, 0, stream>>>(a);
+    else if (c.store_bytes == 8) ragged_kernel<8><<<grid, c.block, 0, stream>>>(a);
+    else ragged_kernel<4><<<grid, c.block, 0, stream>>>(a);
+    return launch_status();
+}
+
+static bool valid_config(const RaggedConfig &c)
+{
+    return (c.block == 64 || c.block == 128 || c.block == 256 || c.block == 512 || c.block == 1024) &&
+           c.chunk_values >= 128 && c.chunk_values % 4 == 0 && c.chunk_values <= (1u << 24) &&
+           (c.store_bytes == 4 || c.store_bytes == 8 || c.store_bytes == 16);
+}
+
+static int ilog2(uint64_t v)
+{
+    int r = 0;
+    while (v > 1) { v >>= 1; ++r; }
+    return r;
+}
+
+// Time candidate configurations on the caller's batch (tables already on the
+// device) and return the fastest.  Each run rewrites the same output bits.
+static orand_status_t autotune(RaggedState *s, const orand_request_t *r, size_t n, char *out, uint64_t out_bytes,
+                               cudaStream_t stream, RaggedConfig *best)
+{
+    static const uint32_t blocks[] = {128, 256, 512};
+    static const uint32_t chunks[] = {2048, 8192, 32768};
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return cuda_status(cudaGetLastError());
+    float best_ms = 1e30f;
+    RaggedConfig cand;
+    orand_status_t st = ORAND_OK;
+    for (uint32_t ch : chunks) {
+        Plan p;
+        if ((st = plan_requests(r, n, out, out_bytes, ch, &p, false)) != ORAND_OK) break;
+        if ((st = ensure_buffers(s, p.table_bytes)) != ORAND_OK) break;
+        cudaEventSynchronize(s->staging_free);
+        write_staging(p, (char *)s->h_staging);
+        cudaError_t e = cudaMemcpyAsync(s->d_tables, s->h_staging, p.table_bytes, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) { st = cuda_status(e); break; }
+        for (uint32_t bl : blocks) {
+            for (uint32_t sw : {16u, 8u}) {
+                cand.block = bl;
+                cand.chunk_values = ch;
+                cand.store_bytes = sw;
+                cand.ctas_per_sm = 0;
+                const RaggedArgs args = make_args(s, p, cand, out);
+                cudaMemsetAsync(args.cursors, 0, 16, stream);
+                cudaEventRecord(a, stream);
+                if ((st = launch_kernel(args, cand, stream)) != ORAND_OK) break;
+                cudaEventRecord(b, stream);
+                e = cudaEventSynchronize(b);
+                if (e != cudaSuccess) { st = cuda_status(e); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                ++s->tune_runs;
+                if (ms < best_ms) { best_ms = ms; *best = cand; }
+            }
+            if (st != ORAND_OK) break;
+        }
+        if (st != ORAND_OK) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    s->have_graph = false;
+    return st;
+}
+
+static bool env_flag(const char *name, bool dflt)
+{
+    const char *v = getenv(name);
+    if (!v || !*v) return dflt;
+    return !(v[0] == '0' || v[0] == 'n' || v[0] == 'N' || v[0] == 'f' || v[0] == 'F');
+}
+
+orand_status_t ragged_serve(orand_ctx_t ctx, const orand_request_t *reqs, size_t n, void *out_base,
+                            uint64_t out_bytes, cudaStream_t stream)
+{
+    orand_status_t st = ctx_check(ctx);
+    if (st != ORAND_OK) return st;
+    if (n == 0) return ORAND_OK;
+    if (reqs == nullptr) return ORAND_ERR_INVALID_ARG;
+    RaggedState *s = state_of(ctx);
+    if (!s) return ORAND_ERR_ALLOC;
+    char *out = (char *)out_base;
+    const bool check_overlap = env_flag("ORAND_CHECK_OVERLAP", false);
+
+    // Validate and plan with the default chunk size; re-plan if the chosen
+    // configuration uses another one.
+    RaggedConfig cfg;
+    Plan plan;
+    if ((st = plan_requests(reqs, n, out, out_bytes, cfg.chunk_values, &plan, check_overlap)) != ORAND_OK)
+        return st;
+    if (plan.total_values == 0) return ORAND_OK;
+    if (out == nullptr) return ORAND_ERR_INVALID_ARG;
+    const auto klass = std::make_tuple(ilog2(plan.total_values), ilog2(n), plan.tyche.empty() ? 0 : 1);
+    if (s->forced) {
+        cfg = s->forced_cfg;
+    } else if (s->tuned.count(klass)) {
+        cfg = s->tuned[klass];
+    } else if (env_flag("ORAND_AUTOTUNE", true)) {
+        if (s->batch_pending) cudaStreamWaitEvent(stream, s->batch_done, 0);
+        if ((st = autotune(s, reqs, n, out, out_bytes, stream, &cfg)) != ORAND_OK) return st;
+        s->tuned[klass] = cfg;
+    }
+    if (cfg.chunk_values != plan.chunk_values &&
+        (st = plan_requests(reqs, n, out, out_bytes, cfg.chunk_values, &plan, false)) != ORAND_OK)
+        return st;
+    if ((st = ensure_buffers(s, plan.table_bytes)) != ORAND_OK) return st;
+
+    // The previous batch's graph must have copied the staging buffer out
+    // before it is rewritten.
+    cudaError_t e = cudaEventSynchronize(s->staging_free);
+    if (e != cudaSuccess) return cuda_status(e);
+    write_staging(plan, (char *)s->h_staging);
+
+    GraphKey key{};
+    key.cfg = cfg;
+    key.n_items = plan.n_items;
+    key.table_bytes = plan.table_bytes;
+    key.n_ty = (uint32_t)plan.tyche.size();
+    key.n = (uint32_t)n;
+    key.out = out;
+    if (!s->have_graph || !(key == s->key)) {
+        if (s->exec) {
+            cudaGraphExecDestroy(s->exec);
+            s->exec = nullptr;
+        }
+        s->have_graph = false;
+        const RaggedArgs args = make_args(s, plan, cfg, out);
+        cudaStream_t cs = s->capture_stream;
+        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_status(e);
+        cudaMemcpyAsync(s->d_tables, s->h_staging, plan.table_bytes, cudaMemcpyHostToDevice, cs);
+        cudaEventRecord(s->staging_free, cs);
+        const orand_status_t lst = launch_kernel(args, cfg, cs);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (lst != ORAND_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return lst;
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaGraphInstantiate(&s->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_status(e);
+        s->key = key;
+        s->have_graph = true;
+        ++s->graph_builds;
+    }
+    if (s->batch_pending && (e = cudaStreamWaitEvent(stream, s->batch_done, 0)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaGraphLaunch(s->exec, stream)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaEventRecord(s->batch_done, stream)) != cudaSuccess) return cuda_status(e);
+    s->batch_pending = true;
+    s->last_cfg = cfg;
+    ++s->graph_launches;
+    return ORAND_OK;
+}
+
+orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uint64_t n_streams, uint64_t dps,
+                           void *out, cudaStream_t stream);
+
+}  // namespace orand_impl
+
+using namespace orand_impl;
+
+extern "C" {
+
+orand_status_t orand_fill_ragged(orand_ctx_t ctx, const orand_request_t *reqs, size_t n, void *out_base,
+                                 uint64_t out_bytes, cudaStream_t stream)
+{
+    return ragged_serve(ctx, reqs, n, out_base, out_bytes, stream);
+}
+
+orand_status_t orand_fill_ragged_serial(const orand_request_t *reqs, size_t n, void *out_base, uint64_t out_bytes,
+                                        cudaStream_t stream)
+{
+    if (n == 0) return ORAND_OK;
+    if (reqs == nullptr) return ORAND_ERR_INVALID_ARG;
+    Plan plan;
+    orand_status_t st = plan_requests(reqs, n, (const char *)out_base, out_bytes, 8192, &plan, false);
+    if (st != ORAND_OK || plan.total_values == 0) return st;
+    if (out_base == nullptr) return ORAND_ERR_INVALID_ARG;
+    for (size_t i = 0; i < n; ++i) {
+        const orand_request_t &q = reqs[i];
+        if (q.length == 0) continue;
+        st = fill_launch((int)q.gen, (int)q.dtype, q.seed, q.counter, 1, q.length,
+                         (char *)out_base + q.out_offset_bytes, stream);
+        if (st != ORAND_OK) return st;
+    }
+    return ORAND_OK;
+}
+
+orand_status_t orand_ragged_set_config(orand_ctx_t ctx, const orand_ragged_config_t *cfg)
+{
+    orand_status_t st = ctx_check(ctx);
+    if (st != ORAND_OK) return st;
+    RaggedState *s = state_of(ctx);
+    if (!s) return ORAND_ERR_ALLOC;
+    if (cfg == nullptr) {
+        s->forced = false;
+        return ORAND_OK;
+    }
+    RaggedConfig c;
+    c.block = cfg->block;
+    c.chunk_values = cfg->chunk_values;
+    c.store_bytes = cfg->store_bytes;
+    c.ctas_per_sm = cfg->ctas_per_sm;
+    if (!valid_config(c)) return ORAND_ERR_INVALID_ARG;
+    s->forced = true;
+    s->forced_cfg = c;
+    return ORAND_OK;
+}
+
+orand_status_t orand_ragged_get_config(orand_ctx_t ctx, orand_ragged_config_t *cfg)
+{
+    orand_status_t st = ctx_check(ctx);
+    if (st != ORAND_OK) return st;
+    if (cfg == nullptr) return ORAND_ERR_INVALID_ARG;
+    RaggedState *s = state_of(ctx);
+    if (!s) return ORAND_ERR_ALLOC;
+    cfg->block = s->last_cfg.block;
+    cfg->chunk_values = s->last_cfg.chunk_values;
+    cfg->store_bytes = s->last_cfg.store_bytes;
+    cfg->ctas_per_sm = s->last_cfg.ctas_per_sm;
+    return ORAND_OK;
+}
+
+orand_status_t orand_ragged_stats(orand_ctx_t ctx, orand_ragged_stats_t *stats)
+{
+    orand_status_t st = ctx_check(ctx);
+    if (st != ORAND_OK) return st;
+    if (stats == nullptr) return ORAND_ERR_INVALID_ARG;
+    RaggedState *s = state_of(ctx);
+    if (!s) return ORAND_ERR_ALLOC;
+    stats->graph_launches = s->graph_launches;
+    stats->graph_builds = s->graph_builds;
+    stats->tune_runs = s->tune_runs;
+    stats->tuned_classes = s->tuned.size();
+    return ORAND_OK;
+}
+
+}  // extern "C"

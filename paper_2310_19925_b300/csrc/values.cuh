@@ -1,0 +1,84 @@
+// Group -> values: the word-to-value maps and the stores shared by the bulk
+// fill and the ragged batcher, so both paths emit identical bits.  A group is
+// four consecutive generator words 4b..4b+3 of one stream; it becomes 4
+// values (u32, FP32 uniform, FP32 normal as two Box-Muller pairs) or 2
+// values (FP64 uniform, high word first).
+#pragma once
+
+#include "orand.h"
+#include "orand_device.cuh"
+
+namespace orand_impl {
+
+// Four words 4b..4b+3 of the stream (key64, counter) for the random-access
+// generators.
+template <int GEN>
+__device__ __forceinline__ uint4 group_words(uint64_t key64, uint32_t counter, uint32_t b)
+{
+    if (GEN == ORAND_PHILOX4x32_10) return orand::philox_block(key64, counter, b);
+    if (GEN == ORAND_THREEFRY4x32_20) return orand::threefry_block(key64, counter, b);
+    return orand::squares_block(orand::squares_key(key64), counter, b);
+}
+
+// Values per group for a dtype.
+template <int DT>
+struct Vals {
+    static constexpr uint32_t V = (DT == ORAND_F64_UNIFORM) ? 2u : 4u;
+};
+
+// The group's values as a 16-byte bit pattern, in memory order: 4 x u32,
+// 4 x f32 (uniform, or normals z0 z1 of pair (w.x, w.y) then of (w.z, w.w)),
+// or 2 x f64 (from (w.x, w.y) and (w.z, w.w)).
+template <int DT>
+__device__ __forceinline__ uint4 group_bits(uint4 w)
+{
+    if (DT == ORAND_U32) return w;
+    if (DT == ORAND_F32_UNIFORM)
+        return make_uint4(__float_as_uint(orand::u01_f32(w.x)), __float_as_uint(orand::u01_f32(w.y)),
+                          __float_as_uint(orand::u01_f32(w.z)), __float_as_uint(orand::u01_f32(w.w)));
+    if (DT == ORAND_F64_UNIFORM) {
+        const unsigned long long a = __double_as_longlong(orand::u01_f64(w.x, w.y));
+        const unsigned long long b = __double_as_longlong(orand::u01_f64(w.z, w.w));
+        return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+    }
+    const float2 p = orand::box_muller_f32(w.x, w.y);
+    const float2 q = orand::box_muller_f32(w.z, w.w);
+    return make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(q.x), __float_as_uint(q.y));
+}
+
+// Masked element stores of a group's bits: values j0 + i for i < V and
+// j0 + i < limit, at dst (the address of value j0).
+template <int DT>
+__device__ __forceinline__ void store_bits_masked(char *dst, uint64_t j0, uint64_t limit, uint4 v)
+{
+    if (DT == ORAND_F64_UNIFORM) {
+        unsigned long long *o = (unsigned long long *)dst;
+        if (j0 < limit) o[0] = ((unsigned long long)v.y << 32) | v.x;
+        if (j0 + 1 < limit) o[1] = ((unsigned long long)v.w << 32) | v.z;
+    } else {
+        uint32_t *o = (uint32_t *)dst;
+        const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (j0 + i < limit) o[i] = e[i];
+    }
+}
+
+// Write the values of group b of stream s.  VEC: one 16-byte store at the
+// group's contiguous slot g.  Otherwise: element stores masked to j < dps.
+template <int DT, bool VEC>
+__device__ __forceinline__ void store_group(void *out, uint64_t g, uint64_t s, uint32_t b, uint64_t dps,
+                                            uint4 w)
+{
+    const uint4 v = group_bits<DT>(w);
+    if (VEC) {
+        reinterpret_cast<uint4 *>(out)[g] = v;
+    } else {
+        constexpr uint32_t V = Vals<DT>::V;
+        constexpr uint32_t E = DT == ORAND_F64_UNIFORM ? 8u : 4u;
+        const uint64_t j0 = (uint64_t)b * V;
+        store_bits_masked<DT>((char *)out + (s * dps + j0) * E, j0, dps, v);
+    }
+}
+
+}  // namespace orand_impl

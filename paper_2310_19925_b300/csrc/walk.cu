@@ -1,0 +1,478 @@
+// Brownian-walk kernels: the fused 2D walk (the paper's macro-benchmark,
+// Fig. 1 and §5, pure-diffusion FP32 form), the differentiable 3D drift walk
+// (forward with checkpoints, noise-regenerating adjoint) and the plain
+// noise-storing one-launch-per-step baseline of the same 3D walk.
+//
+// Fused kernels keep each particle's position and its Philox round keys in
+// registers for the whole walk.  A step is one Philox block, keyed by the
+// particle id with counter (0, t, 0, 0), followed by Box-Muller in FP32 and
+// a compensated update.  Only the start and end touch HBM.  The cost is
+// integer- and FP-pipe work per step, not bytes.
+#include <math.h>
+
+#include "common.cuh"
+#include "ctx.cuh"
+#include "orand_device.cuh"
+
+namespace orand_impl {
+
+constexpr int kWalkBlock = 256;
+constexpr int kRedWidth = 4;  // FP64 partial sums per block: loss or (dmu0..2, dsigma)
+
+// Kahan-compensated x += inc.
+__device__ __forceinline__ void kahan_add(float &x, float &c, float inc)
+{
+    const float y = inc - c;
+    const float t = x + y;
+    c = (t - x) - y;
+    x = t;
+}
+
+// Deterministic block sum of `W` doubles per thread into partials[blockIdx.x * W + j].
+template <int W>
+__device__ __forceinline__ void block_reduce_store(double (&v)[W], double *partials)
+{
+    __shared__ double red[kWalkBlock / 32][W];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        double x = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) red[warp][j] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < W) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWalkBlock / 32; ++w) s += red[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * W + threadIdx.x] = s;
+    }
+}
+
+// Sum the `n` per-block partials of each of W columns in a fixed order,
+// scale by `scale` (and by *gscale if given) and write out[0..W).
+template <int W>
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__restrict__ partials, uint32_t n,
+                                                              double scale, const double *__restrict__ gscale,
+                                                              double *__restrict__ out, int n_out)
+{
+    __shared__ double sh[256];
+    for (int j = 0; j < n_out; ++j) {
+        double s = 0.0;
+        for (uint32_t i = threadIdx.x; i < n; i += 256) s += partials[(size_t)i * W + j];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[j] = sh[0] * scale * (gscale ? *gscale : 1.0);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ 2D walk
+
+__global__ void __launch_bounds__(kWalkBlock) walk2d_kernel(uint64_t n, uint64_t p_first, uint64_t seed,
+                                                           uint32_t steps, float s, float2 *__restrict__ out)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    if (i >= n) return;
+    const orand::PhiloxKeys keys(seed ^ (p_first + i));
+    uint4 w = keys.block(0u, 0u);
+    float x = orand::u01_f32(w.x), y = orand::u01_f32(w.y);
+    float cx = 0.f, cy = 0.f;
+    for (uint32_t t = 1; t <= steps; ++t) {
+        w = keys.block(0u, t);
+        const float2 z = orand::box_muller_f32(w.x, w.y);
+        kahan_add(x, cx, s * z.x);
+        kahan_add(y, cy, s * z.y);
+    }
+    out[i] = make_float2(x, y);
+}
+
+// ------------------------------------------------------------------ 3D walk
+
+struct Walk3dArgs {
+    uint64_t n, p_first, seed;
+    uint32_t steps, K;
+    float mu_dt[3];   // fl32(mu_c * dt)
+    float sig_sqdt;   // fl32(sigma * sqrt(dt))
+    double k_over_p;  // k / p_total
+    double t_dt;      // steps * dt (FP64, exact product of the FP32 dt)
+    double sqdt;      // sqrt(dt) in FP64
+};
+
+__device__ __forceinline__ void walk3d_normals(const orand::PhiloxKeys &keys, uint32_t t_counter, float z[3])
+{
+    const uint4 w = keys.block(0u, t_counter);
+    const float2 a = orand::box_muller_f32(w.x, w.y);
+    z[0] = a.x;
+    z[1] = a.y;
+    z[2] = orand::box_muller_cos_f32(w.z, w.w);
+}
+
+__device__ __forceinline__ void walk3d_x0(const orand::PhiloxKeys &keys, float x[3])
+{
+    const uint4 w = keys.block(0u, 0u);
+    x[0] = 2.0f * orand::u01_f32(w.x) - 1.0f;
+    x[1] = 2.0f * orand::u01_f32(w.y) - 1.0f;
+    x[2] = 2.0f * orand::u01_f32(w.z) - 1.0f;
+}
+
+__global__ void __launch_bounds__(kWalkBlock) walk3d_init_kernel(Walk3dArgs a, float *__restrict__ x0)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    if (i >= a.n) return;
+    const orand::PhiloxKeys keys(a.seed ^ (a.p_first + i));
+    float x[3];
+    walk3d_x0(keys, x);
+    x0[3 * i] = x[0];
+    x0[3 * i + 1] = x[1];
+    x0[3 * i + 2] = x[2];
+}
+
+__global__ void __launch_bounds__(kWalkBlock) walk3d_fwd_kernel(Walk3dArgs a, const float *__restrict__ x0_in,
+                                                               float *__restrict__ xT, float *__restrict__ ckpt,
+                                                               double *__restrict__ partials)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    double loss[kRedWidth] = {0.0, 0.0, 0.0, 0.0};
+    if (i < a.n) {
+        const orand::PhiloxKeys keys(a.seed ^ (a.p_first + i));
+        float x[3], c[3] = {0.f, 0.f, 0.f};
+        if (x0_in) {
+            x[0] = x0_in[3 * i];
+            x[1] = x0_in[3 * i + 1];
+            x[2] = x0_in[3 * i + 2];
+        } else {
+            walk3d_x0(keys, x);
+        }
+        uint32_t next_ck = 0, j = 0;
+        for (uint32_t t = 0; t < a.steps; ++t) {
+            if (ckpt && t == next_ck) {
+                float *dst = ckpt + ((size_t)j * a.n + i) * 3;
+                dst[0] = x[0];
+                dst[1] = x[1];
+                dst[2] = x[2];
+                ++j;
+                next_ck += a.K;
+            }
+            float z[3];
+            walk3d_normals(keys, t + 1u, z);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], fmaf(a.sig_sqdt, z[q], a.mu_dt[q]));
+        }
+        xT[3 * i] = x[0];
+        xT[3 * i + 1] = x[1];
+        xT[3 * i + 2] = x[2];
+        const double r2 = (double)x[0] * x[0] + (double)x[1] * x[1] + (double)x[2] * x[2];
+        loss[0] = 0.5 * r2;
+    }
+    if (partials) block_reduce_store<kRedWidth>(loss, partials);
+}
+
+// Adjoint: lambda = k x_T / p_total * g is constant in time (constant drift).
+// dL/dmu_c = lambda_c * steps * dt, dL/dsigma = sum_c lambda_c sqrt(dt) sum_t z_t,c,
+// with every z_t regenerated from its key, walking time backwards.
+__global__ void __launch_bounds__(kWalkBlock) walk3d_bwd_kernel(Walk3dArgs a, const float *__restrict__ xT,
+                                                               const double *__restrict__ grad_loss,
+                                                               float *__restrict__ dx0,
+                                                               double *__restrict__ partials)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    double g[kRedWidth] = {0.0, 0.0, 0.0, 0.0};
+    if (i < a.n) {
+        const double gl = grad_loss ? *grad_loss : 1.0;
+        const orand::PhiloxKeys keys(a.seed ^ (a.p_first + i));
+        double lam[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) lam[q] = a.k_over_p * (double)xT[3 * i + q] * gl;
+        float S[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+        for (uint32_t tt = a.steps; tt > 0; --tt) {
+            float z[3];
+            walk3d_normals(keys, tt, z);   // z_{tt-1} uses counter tt
+#pragma unroll
+            for (int q = 0; q < 3; ++q) kahan_add(S[q], c[q], z[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            g[q] = lam[q] * a.t_dt;
+            g[3] += lam[q] * a.sqdt * (double)S[q];
+            if (dx0) dx0[3 * i + q] = (float)lam[q];
+        }
+    }
+    block_reduce_store<kRedWidth>(g, partials);
+}
+
+// ------------------------------------------- plain noise-storing baseline
+
+__global__ void __launch_bounds__(kWalkBlock) plain_init_kernel(Walk3dArgs a, const float *__restrict__ x0_in,
+                                                               float *__restrict__ x)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    if (i >= a.n) return;
+    if (x0_in) {
+        for (int q = 0; q < 3; ++q) x[3 * i + q] = x0_in[3 * i + q];
+    } else {
+        const orand::PhiloxKeys keys(a.seed ^ (a.p_first + i));
+        float v[3];
+        walk3d_x0(keys, v);
+        for (int q = 0; q < 3; ++q) x[3 * i + q] = v[q];
+    }
+}
+
+// One step of the walk for all particles: regenerate the key (state
+// construction per launch, as in the paper's listing), draw z_t, store it,
+// update x in HBM.
+__global__ void __launch_bounds__(kWalkBlock) plain_step_kernel(Walk3dArgs a, uint32_t t, float *__restrict__ x,
+                                                               float *__restrict__ z_t)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    if (i >= a.n) return;
+    const uint64_t key64 = a.seed ^ (a.p_first + i);
+    const uint4 w = orand::philox_block(key64, t + 1u, 0u);
+    const float2 p = orand::box_muller_f32(w.x, w.y);
+    const float z[3] = {p.x, p.y, orand::box_muller_cos_f32(w.z, w.w)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        z_t[3 * i + q] = z[q];
+        x[3 * i + q] = x[3 * i + q] + fmaf(a.sig_sqdt, z[q], a.mu_dt[q]);
+    }
+}
+
+__global__ void __launch_bounds__(kWalkBlock) plain_loss_kernel(Walk3dArgs a, const float *__restrict__ x,
+                                                               double *__restrict__ partials)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    double v[kRedWidth] = {0.0, 0.0, 0.0, 0.0};
+    if (i < a.n) {
+        const double r2 = (double)x[3 * i] * x[3 * i] + (double)x[3 * i + 1] * x[3 * i + 1] +
+                          (double)x[3 * i + 2] * x[3 * i + 2];
+        v[0] = 0.5 * r2;
+    }
+    block_reduce_store<kRedWidth>(v, partials);
+}
+
+// Backward, one launch per step: S += z_t read back from HBM.
+__global__ void __launch_bounds__(kWalkBlock) plain_bwd_step_kernel(uint64_t n3, const float *__restrict__ z_t,
+                                                                   float *__restrict__ S)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    if (i < n3) S[i] += z_t[i];
+}
+
+__global__ void __launch_bounds__(kWalkBlock) plain_bwd_final_kernel(Walk3dArgs a, const float *__restrict__ xT,
+                                                                    const float *__restrict__ S,
+                                                                    const double *__restrict__ grad_loss,
+                                                                    float *__restrict__ dx0,
+                                                                    double *__restrict__ partials)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    double g[kRedWidth] = {0.0, 0.0, 0.0, 0.0};
+    if (i < a.n) {
+        const double gl = grad_loss ? *grad_loss : 1.0;
+        for (int q = 0; q < 3; ++q) {
+            const double lam = a.k_over_p * (double)xT[3 * i + q] * gl;
+            g[q] = lam * a.t_dt;
+            g[3] += lam * a.sqdt * (double)S[3 * i + q];
+            if (dx0) dx0[3 * i + q] = (float)lam;
+        }
+    }
+    block_reduce_store<kRedWidth>(g, partials);
+}
+
+// ------------------------------------------------------------ host side
+
+static unsigned walk_grid(uint64_t n) { return (unsigned)ceil_div(n, kWalkBlock); }
+
+// One particle per thread: the grid must fit the 2^31 - 1 block limit.
+static bool walk_grid_ok(uint64_t n) { return ceil_div(n, kWalkBlock) <= 0x7FFFFFFFull; }
+
+static bool finite_nonneg(float v) { return isfinite(v) && v >= 0.0f; }
+
+static orand_status_t walk3d_args(const orand_walk3d_t *p, Walk3dArgs *a)
+{
+    if (p == nullptr) return ORAND_ERR_INVALID_ARG;
+    if (!finite_nonneg(p->dt) || !finite_nonneg(p->sigma) || !isfinite(p->k) || !isfinite(p->mu[0]) ||
+        !isfinite(p->mu[1]) || !isfinite(p->mu[2]))
+        return ORAND_ERR_INVALID_ARG;
+    if (p->p_first + p->n_particles < p->p_first) return ORAND_ERR_OVERFLOW;
+    if (!walk_grid_ok(p->n_particles)) return ORAND_ERR_OVERFLOW;
+    if (p->steps == UINT32_MAX) return ORAND_ERR_OVERFLOW;  // counters t + 1 must fit 32 bits
+    a->n = p->n_particles;
+    a->p_first = p->p_first;
+    a->seed = p->seed;
+    a->steps = p->steps;
+    a->K = p->ckpt_every;
+    const double dt = (double)p->dt;
+    for (int q = 0; q < 3; ++q) a->mu_dt[q] = (float)((double)p->mu[q] * dt);
+    a->sig_sqdt = (float)((double)p->sigma * sqrt(dt));
+    const double P = (double)(p->p_total ? p->p_total : p->n_particles);
+    a->k_over_p = P > 0 ? (double)p->k / P : 0.0;
+    a->t_dt = (double)p->steps * dt;
+    a->sqdt = sqrt(dt);
+    return ORAND_OK;
+}
+
+
+
+static orand_status_t check_ptr(const void *ptr, size_t align)
+{
+    if (ptr == nullptr) return ORAND_ERR_INVALID_ARG;
+    return ((uintptr_t)ptr % align) ? ORAND_ERR_ALIGNMENT : ORAND_OK;
+}
+
+}  // namespace orand_impl
+
+using namespace orand_impl;
+
+extern "C" {
+
+orand_status_t orand_brownian_walk(const orand_walk2d_t *p, float *pos_out, cudaStream_t stream)
+{
+    if (p == nullptr) return ORAND_ERR_INVALID_ARG;
+    if (!finite_nonneg(p->dt) || !finite_nonneg(p->D)) return ORAND_ERR_INVALID_ARG;
+    if (p->p_first + p->n_particles < p->p_first) return ORAND_ERR_OVERFLOW;
+    if (p->n_particles > UINT64_MAX / 8) return ORAND_ERR_OVERFLOW;
+    if (p->n_particles == 0) return ORAND_OK;
+    orand_status_t st = check_ptr(pos_out, 8);
+    if (st != ORAND_OK) return st;
+    if (!walk_grid_ok(p->n_particles)) return ORAND_ERR_OVERFLOW;
+    DeviceInfo info;
+    if ((st = current_device(&info)) != ORAND_OK) return st;
+    const float s = (float)sqrt(2.0 * (double)p->D * (double)p->dt);
+    walk2d_kernel<<<walk_grid(p->n_particles), kWalkBlock, 0, stream>>>(p->n_particles, p->p_first, p->seed,
+                                                                      p->steps, s, (float2 *)pos_out);
+    return launch_status();
+}
+
+orand_status_t orand_walk3d_init(const orand_walk3d_t *p, float *x0, cudaStream_t stream)
+{
+    Walk3dArgs a;
+    orand_status_t st = walk3d_args(p, &a);
+    if (st != ORAND_OK || a.n == 0) return st;
+    if ((st = check_ptr(x0, 4)) != ORAND_OK) return st;
+    DeviceInfo info;
+    if ((st = current_device(&info)) != ORAND_OK) return st;
+    walk3d_init_kernel<<<walk_grid(a.n), kWalkBlock, 0, stream>>>(a, x0);
+    return launch_status();
+}
+
+orand_status_t orand_walk3d_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *xT,
+                                float *ckpt, double *loss, cudaStream_t stream)
+{
+    Walk3dArgs a;
+    orand_status_t st = walk3d_args(p, &a);
+    if (st != ORAND_OK) return st;
+    if ((st = ctx_check(ctx)) != ORAND_OK) return st;
+    if (a.n == 0) {
+        if (loss) return cuda_status(cudaMemsetAsync(loss, 0, sizeof(double), stream));
+        return ORAND_OK;
+    }
+    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
+    if (x0 && ((uintptr_t)x0 % 4)) return ORAND_ERR_ALIGNMENT;
+    if (ckpt && ((uintptr_t)ckpt % 4)) return ORAND_ERR_ALIGNMENT;
+    if (loss && ((uintptr_t)loss % 8)) return ORAND_ERR_ALIGNMENT;
+    if (a.K == 0) ckpt = nullptr;
+    const unsigned grid = walk_grid(a.n);
+    double *partials = nullptr;
+    if (loss) {
+        void *scr = nullptr;
+        if ((st = ctx_scratch(ctx, (size_t)grid * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
+        partials = (double *)scr;
+    }
+    walk3d_fwd_kernel<<<grid, kWalkBlock, 0, stream>>>(a, x0, xT, ckpt, partials);
+    if ((st = launch_status()) != ORAND_OK || !loss) return st;
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, a.k_over_p, nullptr, loss, 1);
+    return launch_status();
+}
+
+orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
+                                const double *grad_loss, double *dmu, double *dsigma, float *dx0,
+                                cudaStream_t stream)
+{
+    Walk3dArgs a;
+    orand_status_t st = walk3d_args(p, &a);
+    if (st != ORAND_OK) return st;
+    if ((st = ctx_check(ctx)) != ORAND_OK) return st;
+    if ((st = check_ptr(dmu, 8)) != ORAND_OK || (st = check_ptr(dsigma, 8)) != ORAND_OK) return st;
+    if (a.n == 0) {
+        cudaError_t e = cudaMemsetAsync(dmu, 0, 3 * sizeof(double), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dsigma, 0, sizeof(double), stream);
+        return cuda_status(e);
+    }
+    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
+    if (dx0 && ((uintptr_t)dx0 % 4)) return ORAND_ERR_ALIGNMENT;
+    if (grad_loss && ((uintptr_t)grad_loss % 8)) return ORAND_ERR_ALIGNMENT;
+    const unsigned grid = walk_grid(a.n);
+    void *scr = nullptr;
+    if ((st = ctx_scratch(ctx, (size_t)grid * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
+    double *partials = (double *)scr;
+    walk3d_bwd_kernel<<<grid, kWalkBlock, 0, stream>>>(a, xT, grad_loss, dx0, partials);
+    if ((st = launch_status()) != ORAND_OK) return st;
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
+    return launch_status();
+}
+
+orand_status_t orand_walk3d_plain_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *x,
+                                      float *z_store, double *loss, cudaStream_t stream)
+{
+    Walk3dArgs a;
+    orand_status_t st = walk3d_args(p, &a);
+    if (st != ORAND_OK) return st;
+    if ((st = ctx_check(ctx)) != ORAND_OK) return st;
+    if (a.n == 0) return ORAND_OK;
+    if ((st = check_ptr(x, 4)) != ORAND_OK) return st;
+    if (a.steps && (st = check_ptr(z_store, 4)) != ORAND_OK) return st;
+    if (x0 && ((uintptr_t)x0 % 4)) return ORAND_ERR_ALIGNMENT;
+    if (loss && ((uintptr_t)loss % 8)) return ORAND_ERR_ALIGNMENT;
+    const unsigned grid = walk_grid(a.n);
+    plain_init_kernel<<<grid, kWalkBlock, 0, stream>>>(a, x0, x);
+    for (uint32_t t = 0; t < a.steps; ++t)
+        plain_step_kernel<<<grid, kWalkBlock, 0, stream>>>(a, t, x, z_store + (size_t)t * a.n * 3);
+    if ((st = launch_status()) != ORAND_OK || !loss) return st;
+    void *scr = nullptr;
+    if ((st = ctx_scratch(ctx, (size_t)grid * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
+    plain_loss_kernel<<<grid, kWalkBlock, 0, stream>>>(a, x, (double *)scr);
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>((double *)scr, grid, a.k_over_p, nullptr, loss, 1);
+    return launch_status();
+}
+
+orand_status_t orand_walk3d_plain_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
+                                      const float *z_store, const double *grad_loss, double *dmu,
+                                      double *dsigma, float *dx0, cudaStream_t stream)
+{
+    Walk3dArgs a;
+    orand_status_t st = walk3d_args(p, &a);
+    if (st != ORAND_OK) return st;
+    if ((st = ctx_check(ctx)) != ORAND_OK) return st;
+    if ((st = check_ptr(dmu, 8)) != ORAND_OK || (st = check_ptr(dsigma, 8)) != ORAND_OK) return st;
+    if (a.n == 0) {
+        cudaError_t e = cudaMemsetAsync(dmu, 0, 3 * sizeof(double), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dsigma, 0, sizeof(double), stream);
+        return cuda_status(e);
+    }
+    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
+    if (a.steps && (st = check_ptr(z_store, 4)) != ORAND_OK) return st;
+    const unsigned grid = walk_grid(a.n);
+    const size_t s_bytes = (a.n * 3 * sizeof(float) + 255) & ~(size_t)255;
+    void *scr = nullptr;
+    if ((st = ctx_scratch(ctx, s_bytes + (size_t)grid * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
+    float *S = (float *)scr;
+    double *partials = (double *)((char *)scr + s_bytes);
+    cudaError_t e = cudaMemsetAsync(S, 0, a.n * 3 * sizeof(float), stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const uint64_t n3 = a.n * 3;
+    const unsigned g3 = (unsigned)ceil_div(n3, kWalkBlock);
+    for (uint32_t tt = a.steps; tt > 0; --tt)
+        plain_bwd_step_kernel<<<g3, kWalkBlock, 0, stream>>>(n3, z_store + (size_t)(tt - 1) * n3, S);
+    plain_bwd_final_kernel<<<grid, kWalkBlock, 0, stream>>>(a, xT, S, grad_loss, dx0, partials);
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
+    return launch_status();
+}
+
+}  // extern "C"

@@ -69,3 +69,37 @@ def test_empty_fill_is_a_noop(lib):
 def test_python_errors_raise(lib):
     with pytest.raises(orand.OrandError):
         orand.orand_fill(9, 0, 1, 0, 1, 1, 16, 0)
+
+
+def test_walk_arguments_rejected_on_host(lib):
+    W2 = orand.walk2d_params
+    assert lib.orand_brownian_walk(None, None, None) == -1
+    assert lib.orand_brownian_walk(ctypes.byref(W2(0, 10)), None, None) == 0            # empty: no-op
+    assert lib.orand_brownian_walk(ctypes.byref(W2(4, 10, dt=-1.0)), None, None) == -1
+    assert lib.orand_brownian_walk(ctypes.byref(W2(4, 10, D=float("nan"))), None, None) == -1
+    assert lib.orand_brownian_walk(ctypes.byref(W2(4, 10)), None, None) == -1           # NULL output
+    assert lib.orand_brownian_walk(ctypes.byref(W2(4, 10)), 4, None) == -3              # not 8-byte aligned
+    assert lib.orand_brownian_walk(ctypes.byref(W2(8, 10, p_first=2**64 - 4)), 8, None) == -2
+    p3 = orand.walk3d_params(10, 5)
+    assert lib.orand_walk3d_fwd(None, ctypes.byref(p3), None, 16, None, None, None) == -1  # no context
+    assert lib.orand_walk3d_fwd(None, None, None, 16, None, None, None) == -1
+    bad = orand.walk3d_params(10, 5, sigma=-0.5)
+    assert lib.orand_walk3d_bwd(None, ctypes.byref(bad), 16, None, 16, 16, None, None) == -1
+    big = orand.walk3d_params(2**40, 5)
+    assert lib.orand_walk3d_init(ctypes.byref(big), 16, None) == -2                      # grid too large
+    steps_max = orand.walk3d_params(1, 2**32 - 1)
+    assert lib.orand_walk3d_init(ctypes.byref(steps_max), 16, None) == -2
+
+
+def test_context_needs_a_device_or_succeeds(lib):
+    import torch
+
+    h = ctypes.c_void_p()
+    st = lib.orand_ctx_create(ctypes.byref(h))
+    if torch.cuda.is_available():
+        assert st == 0 and h.value
+        assert lib.orand_ctx_destroy(h) == 0
+    else:
+        assert st in (-5, -7) and not h.value
+    assert lib.orand_ctx_create(None) == -1
+    assert lib.orand_ctx_destroy(None) == -1

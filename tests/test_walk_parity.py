@@ -1,0 +1,225 @@
+"""GPU parity of the walk kernels against the FP64 CPU oracle.
+
+Bars: walk positions |gpu - oracle| <= 1e-5 * max(|oracle|, 1) (FP32 with
+compensated summation vs FP64); initial positions bit-exact; loss and
+gradients within 1e-3 relative (they come out near 1e-6).  Full-size
+workloads (2^24 x 10^4 2D, 2^22 x 4096 3D) run in the benchmark's launch
+configuration and are checked on sampled particles, on particle-range
+subsets, and by properties that hold at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import to_numpy
+
+import paper_2310_19925_b300 as orand
+from paper_2310_19925_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def pos_close(gpu, ref):
+    err = np.abs(gpu.astype(np.float64) - ref)
+    bound = POS_TOL * np.maximum(np.abs(ref), 1.0)
+    assert np.all(err <= bound), "worst %.3g (bound %.3g)" % ((err / bound).max(), POS_TOL)
+
+
+# ------------------------------------------------------------------- 2D ----
+
+@pytest.mark.parametrize("steps", [0, 1, 37, 1000])
+@pytest.mark.parametrize("p_first", [0, 2**40 + 5])
+def test_walk2d_small(torch_cuda, orc, steps, p_first):
+    n = 1000
+    f32 = lambda v: float(np.float32(v))
+    got = to_numpy(orand.brownian_walk(n, steps, dt=1e-3, D=1.0, seed=0x77, p_first=p_first))
+    x0, xT = orc.walk2d(0x77, n, steps, f32(1e-3), 1.0, p_first=p_first, threads=8)
+    if steps == 0:
+        assert np.array_equal(got.astype(np.float64), x0)
+    pos_close(got, xT)
+
+
+def test_walk2d_full_workload_sampled(torch_cuda, orc):
+    c = W.WALK2D
+    got = orand.brownian_walk(c["n_particles"], c["steps"], c["dt"], c["D"], c["seed"])
+    torch_cuda.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    ids = np.unique(np.concatenate([[0, c["n_particles"] - 1], rng.integers(0, c["n_particles"], 62)]))
+    g = to_numpy(got)
+    for p in ids:
+        _, xT = orc.walk2d(c["seed"], 1, c["steps"], float(np.float32(c["dt"])), c["D"], p_first=int(p))
+        pos_close(g[p:p + 1], xT)
+    # Einstein relation over all 2^24 particles: Var(x_T - x_0) = 2 D T dt.
+    d = got.double() - 0.5
+    var = (d.var(dim=0) - 1.0 / 12.0).cpu().numpy()
+    expect = 2 * c["D"] * c["steps"] * float(np.float32(c["dt"]))
+    assert np.all(np.abs(var / expect - 1) < 5 * math.sqrt(2 / c["n_particles"]) * 1.2)
+
+
+# ------------------------------------------------------------------- 3D ----
+
+MU = (0.1, -0.2, 0.05)
+
+
+def _p(n, steps, K=16, p_first=0, p_total=0, seed=0, mu=MU, sigma=0.5):
+    return orand.walk3d_params(n, steps, dt=1e-3, mu=mu, sigma=sigma, k=2.0, seed=seed, ckpt_every=K,
+                               p_first=p_first, p_total=p_total)
+
+
+def _f32(v):
+    return float(np.float32(v))
+
+
+@pytest.mark.parametrize("n,steps,K", [(1, 1, 1), (777, 200, 16), (300, 65, 64), (513, 0, 8)])
+def test_walk3d_forward_small(torch_cuda, orc, n, steps, K):
+    p = _p(n, steps, K, p_first=3)
+    x0 = orand.walk3d_init(p)
+    xT, ck, loss = orand.walk3d_forward(p)
+    xT2, ck2, loss2 = orand.walk3d_forward(p, x0=x0)
+    torch_cuda.cuda.synchronize()
+    ox0 = orc.walk3d_init(0, n, p_first=3)
+    oxT, ock = orc.walk3d_forward(0, n, steps, K, _f32(1e-3), MU, 0.5, p_first=3, want_ckpt=True)
+    assert np.array_equal(to_numpy(x0).astype(np.float64), ox0)
+    pos_close(to_numpy(xT), oxT)
+    assert torch_cuda.equal(xT, xT2) and loss.item() == loss2.item()
+    if ock.shape[0]:
+        pos_close(to_numpy(ck), ock)
+        assert torch_cuda.equal(ck, ck2)
+    else:
+        assert ck is None
+    oloss = orc.walk3d_loss(oxT, 2.0, n)
+    assert loss.item() == pytest.approx(oloss, rel=GRAD_TOL, abs=1e-12)
+
+
+@pytest.mark.parametrize("n,steps", [(1, 3), (777, 200), (1024, 64)])
+def test_walk3d_adjoint_small(torch_cuda, orc, n, steps):
+    p = _p(n, steps, p_first=11, p_total=5 * n)
+    xT, _, _ = orand.walk3d_forward(p, want_ckpt=False)
+    g = torch_cuda.tensor(0.75, dtype=torch_cuda.float64, device="cuda")
+    dmu, dsig, dx0 = orand.walk3d_backward(p, xT, g)
+    torch_cuda.cuda.synchronize()
+    oxT, _ = orc.walk3d_forward(0, n, steps, 16, _f32(1e-3), MU, 0.5, p_first=11)
+    odmu, odsig, odx0 = orc.walk3d_adjoint(0, n, steps, _f32(1e-3), oxT, 2.0, 5 * n, p_first=11)
+    assert np.allclose(to_numpy(dmu), 0.75 * odmu, rtol=GRAD_TOL, atol=0)
+    assert dsig.item() == pytest.approx(0.75 * odsig, rel=GRAD_TOL)
+    np.testing.assert_allclose(to_numpy(dx0), 0.75 * odx0, rtol=GRAD_TOL, atol=1e-12)
+
+
+def test_walk3d_autograd_function(torch_cuda, orc):
+    torch = torch_cuda
+    n, steps = 2048, 128
+    BW = orand.BrownianWalk3D()
+    p = _p(n, steps, K=32)
+    x0 = orand.walk3d_init(p).requires_grad_(True)
+    mu = torch.tensor(MU, dtype=torch.float32, requires_grad=True)
+    sigma = torch.tensor(0.5, dtype=torch.float32, requires_grad=True)
+    loss = BW.apply(mu, sigma, x0, steps, 1e-3, 2.0, 0, 32)
+    loss.backward()
+    assert BW.last_checkpoints.shape == (4, n, 3)
+    oxT, _ = orc.walk3d_forward(0, n, steps, 32, _f32(1e-3), MU, 0.5)
+    odmu, odsig, odx0 = orc.walk3d_adjoint(0, n, steps, _f32(1e-3), oxT, 2.0, n)
+    assert loss.item() == pytest.approx(orc.walk3d_loss(oxT, 2.0, n), rel=1e-6)
+    assert np.allclose(mu.grad.numpy(), odmu, rtol=GRAD_TOL)
+    assert sigma.grad.item() == pytest.approx(odsig, rel=GRAD_TOL)
+    np.testing.assert_allclose(to_numpy(x0.grad), odx0, rtol=GRAD_TOL)
+    # Central differences through the GPU forward agree with the adjoint.
+    h = 1e-3
+    with torch.no_grad():
+        lp = BW.apply(mu, sigma + h, x0, steps, 1e-3, 2.0, 0, 32).item()
+        lm = BW.apply(mu, sigma - h, x0, steps, 1e-3, 2.0, 0, 32).item()
+    sp, sm = _f32(_f32(0.5) + h), _f32(_f32(0.5) - h)
+    assert (lp - lm) / (sp - sm) == pytest.approx(sigma.grad.item(), rel=GRAD_TOL)
+
+
+def test_walk3d_plain_baseline_matches_fused(torch_cuda):
+    torch = torch_cuda
+    n, steps = 4096, 100
+    p = _p(n, steps)
+    ctx = orand.default_context().handle
+    sh = torch.cuda.current_stream().cuda_stream
+    xT, _, loss = orand.walk3d_forward(p, want_ckpt=False)
+    dmu, dsig, dx0 = orand.walk3d_backward(p, xT)
+    x = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    z = torch.empty((steps, n, 3), dtype=torch.float32, device="cuda")
+    ploss = torch.empty((), dtype=torch.float64, device="cuda")
+    orand.orand_walk3d_plain_fwd(ctx, p, 0, x.data_ptr(), z.data_ptr(), ploss.data_ptr(), sh)
+    pdmu = torch.empty(3, dtype=torch.float64, device="cuda")
+    pdsig = torch.empty((), dtype=torch.float64, device="cuda")
+    pdx0 = torch.empty_like(x)
+    orand.orand_walk3d_plain_bwd(ctx, p, x.data_ptr(), z.data_ptr(), 0, pdmu.data_ptr(), pdsig.data_ptr(),
+                                 pdx0.data_ptr(), sh)
+    torch.cuda.synchronize()
+    assert torch.allclose(x, xT, rtol=POS_TOL, atol=POS_TOL)
+    assert ploss.item() == pytest.approx(loss.item(), rel=GRAD_TOL)
+    assert torch.allclose(pdmu, dmu, rtol=GRAD_TOL) and pdsig.item() == pytest.approx(dsig.item(), rel=GRAD_TOL)
+    assert torch.allclose(pdx0, dx0, rtol=GRAD_TOL)
+    # The stored noise is exactly what the fused kernels regenerate: z_0 drives x_1.
+    p1 = _p(n, 1)
+    x1, _, _ = orand.walk3d_forward(p1, want_ckpt=False)
+    x0 = orand.walk3d_init(p1)
+    inc = (x1 - x0).double()
+    mu_dt = torch.tensor([_f32(m * _f32(1e-3)) for m in MU], dtype=torch.float64, device="cuda")
+    zz = (inc - mu_dt) / _f32(0.5 * math.sqrt(_f32(1e-3)))
+    assert torch.allclose(zz, z[0].double(), atol=1e-4)
+
+
+def test_walk3d_full_workload(torch_cuda, orc):
+    """2^22 x 4096 forward + adjoint: sampled particles against the oracle,
+    a particle-range subset of the reductions against the oracle adjoint,
+    and loss/dmu/dsigma by properties of the full run."""
+    torch = torch_cuda
+    c = W.WALK3D
+    P, T = c["n_particles"], c["steps"]
+    p = orand.walk3d_params(P, T, c["dt"], c["mu"], c["sigma"], c["k"], c["seed"], c["ckpt_every"])
+    xT, ck, loss = orand.walk3d_forward(p)
+    dmu, dsig, dx0 = orand.walk3d_backward(p, xT)
+    torch.cuda.synchronize()
+    assert ck.shape == (T // c["ckpt_every"], P, 3)
+    rng = np.random.default_rng(9)
+    ids = np.unique(np.concatenate([[0, P - 1], rng.integers(0, P, 30)]))
+    dt32 = _f32(c["dt"])
+    gx, gdx = to_numpy(xT), to_numpy(dx0)
+    for q in ids:
+        oxT, ock = orc.walk3d_forward(c["seed"], 1, T, c["ckpt_every"], dt32, c["mu"], c["sigma"], p_first=int(q),
+                                      want_ckpt=True)
+        pos_close(gx[q:q + 1], oxT)
+        pos_close(to_numpy(ck[:, q]), ock[:, 0])
+        np.testing.assert_allclose(gdx[q], c["k"] * oxT[0] / P, rtol=GRAD_TOL)
+    # Properties of the full run (exact identities of the linear walk).
+    x64 = xT.double()
+    assert loss.item() == pytest.approx(0.5 * c["k"] * (x64 ** 2).sum().item() / P, rel=1e-9)
+    assert np.allclose(to_numpy(dmu), c["k"] * T * dt32 * x64.mean(dim=0).cpu().numpy(), rtol=1e-6)
+    assert np.allclose(to_numpy(dmu), [3.35, -6.7, 1.68], rtol=0.05)
+    assert dsig.item() == pytest.approx(12.3, rel=0.05)
+    # A particle-range subset of the reductions against the FP64 oracle adjoint.
+    sub = orand.walk3d_params(1024, T, c["dt"], c["mu"], c["sigma"], c["k"], c["seed"], c["ckpt_every"],
+                              p_first=123456, p_total=P)
+    sxT, _, _ = orand.walk3d_forward(sub, want_ckpt=False)
+    sdmu, sdsig, _ = orand.walk3d_backward(sub, sxT)
+    oxT, _ = orc.walk3d_forward(c["seed"], 1024, T, 64, dt32, c["mu"], c["sigma"], p_first=123456, threads=8)
+    odmu, odsig, _ = orc.walk3d_adjoint(c["seed"], 1024, T, dt32, oxT, c["k"], P, p_first=123456, threads=8)
+    assert np.allclose(to_numpy(sdmu), odmu, rtol=GRAD_TOL)
+    assert sdsig.item() == pytest.approx(odsig, rel=GRAD_TOL)
+    # Central differences (h = 1e-3) on the GPU forward: exact for the quadratic loss.
+    h = 1e-3
+    lp = orand.walk3d_forward(orand.walk3d_params(P, T, c["dt"], c["mu"], c["sigma"] + h, c["k"], c["seed"], 0),
+                              want_ckpt=False)[2].item()
+    lm = orand.walk3d_forward(orand.walk3d_params(P, T, c["dt"], c["mu"], c["sigma"] - h, c["k"], c["seed"], 0),
+                              want_ckpt=False)[2].item()
+    sp, sm = _f32(_f32(c["sigma"]) + h), _f32(_f32(c["sigma"]) - h)
+    assert (lp - lm) / (sp - sm) == pytest.approx(dsig.item(), rel=GRAD_TOL)
+    del xT, ck, dx0
+    torch.cuda.empty_cache()
