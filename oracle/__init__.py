@@ -72,6 +72,9 @@ def lib():
         L.orc_f64_uniform.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
         L.orc_f64_uniform.restype = ctypes.c_double
         L.orc_box_muller.argtypes = [ctypes.c_uint32, ctypes.c_uint32, dp]
+        L.orc_box_muller_array.argtypes = [u32p, u32p, ctypes.c_uint64, dp]
+        L.orc_map_words.argtypes = [ctypes.c_int, u32p, ctypes.c_uint64, ctypes.c_void_p]
+        L.orc_map_words.restype = ctypes.c_int
         L.orc_fill.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                ctypes.c_void_p, u32p]
@@ -168,6 +171,25 @@ def box_muller(w0: int, w1: int):
     z = np.zeros(2, np.float64)
     lib().orc_box_muller(w0 & 0xFFFFFFFF, w1 & 0xFFFFFFFF, _dp(z))
     return float(z[0]), float(z[1])
+
+
+def box_muller_array(w0, w1) -> np.ndarray:
+    """Box-Muller of word pairs: returns (n, 2) float64."""
+    a = np.ascontiguousarray(w0, np.uint32)
+    b = np.ascontiguousarray(w1, np.uint32)
+    z = np.zeros((len(a), 2), np.float64)
+    lib().orc_box_muller_array(_u32p(a), _u32p(b), len(a), _dp(z))
+    return z
+
+
+def map_words(dtype: int, words) -> np.ndarray:
+    """Apply a dtype's word->value map to a word array (uint32 or float64 out)."""
+    w = np.ascontiguousarray(words, np.uint32)
+    n = len(w) // 2 if dtype == F64_UNIFORM else len(w)
+    out = np.zeros(n, np.uint32 if dtype == U32 else np.float64)
+    if n and lib().orc_map_words(dtype, _u32p(w), n, out.ctypes.data_as(ctypes.c_void_p)) != 0:
+        raise ValueError("oracle: bad dtype")
+    return out
 
 
 def words_for(dtype: int, dps: int) -> int:

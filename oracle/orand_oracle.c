@@ -242,7 +242,8 @@ int orc_stream_words(int gen, uint64_t key64, uint32_t counter, uint64_t first, 
  *                 exact, in [0, 1).
  *   Box-Muller:   u1 = ((w0 >> 8) + 1) * 2^-24 in (0, 1],
  *                 u2 = (w1 >> 8) * 2^-24 in [0, 1);
- *                 r = sqrt(-2 ln u1); z0 = r cos(2 pi u2), z1 = r sin(2 pi u2).
+ *                 r = sqrt(-2 ln u1); z0 = r cos(2 pi u2), z1 = r sin(2 pi u2),
+ *                 the trigonometric pair taken by exact quadrant reduction.
  * ---------------------------------------------------------------------- */
 double orc_f32_uniform(uint32_t w) { return ldexp((double)(w >> 8), -24); }
 
@@ -252,14 +253,66 @@ double orc_f64_uniform(uint32_t hi, uint32_t lo)
     return ldexp((double)(v >> 11), -53);
 }
 
+/* cos(2 pi u2) and sin(2 pi u2) for u2 in [0, 1), by the exact quadrant
+ * identity: with y = 4 u2 (exact), q = nearest integer to y and
+ * t = y - q in [-1/2, 1/2] (exact), 2 pi u2 = (pi/2) q + (pi/2) t, so the pair
+ * is a signed swap of (cos, sin)((pi/2) t) chosen by q mod 4.  Where the
+ * exact value is 0 (u2 a multiple of 1/4) this gives exactly 0, which a
+ * direct cos(2*pi*u2) in FP64 does not. */
+static void cos_sin_2pi(double u2, double *c, double *s)
+{
+    const double half_pi = 1.5707963267948966192313216916398;
+    const double y = 4.0 * u2;
+    const double q = floor(y + 0.5);
+    const double t = y - q;
+    const double ct = cos(half_pi * t), st = sin(half_pi * t);
+    switch (((long)q) & 3) {
+    case 0: *c = ct; *s = st; break;
+    case 1: *c = -st; *s = ct; break;
+    case 2: *c = -ct; *s = -st; break;
+    default: *c = st; *s = -ct; break;
+    }
+}
+
 void orc_box_muller(uint32_t w0, uint32_t w1, double z[2])
 {
-    const double two_pi = 6.283185307179586476925286766559;
     double u1 = ldexp((double)((w0 >> 8) + 1u), -24);
     double u2 = ldexp((double)(w1 >> 8), -24);
     double r = sqrt(-2.0 * log(u1));
-    z[0] = r * cos(two_pi * u2);
-    z[1] = r * sin(two_pi * u2);
+    double c, s;
+    cos_sin_2pi(u2, &c, &s);
+    z[0] = r * c;
+    z[1] = r * s;
+}
+
+/* Box-Muller over arrays of word pairs: z[2i], z[2i+1] from (w0[i], w1[i]). */
+void orc_box_muller_array(const uint32_t *w0, const uint32_t *w1, uint64_t n, double *z)
+{
+    for (uint64_t i = 0; i < n; ++i) orc_box_muller(w0[i], w1[i], z + 2 * i);
+}
+
+/* Word -> value map over an array of words, as the fills apply it: u32
+ * copies, FP32 uniform per word, FP64 uniform per word pair (first high),
+ * FP32 normal per word pair.  n_values values are written (as uint32 or
+ * double). */
+int orc_map_words(int dtype, const uint32_t *w, uint64_t n_values, void *out)
+{
+    for (uint64_t j = 0; j < n_values; ++j) {
+        if (dtype == ORC_U32) {
+            ((uint32_t *)out)[j] = w[j];
+        } else if (dtype == ORC_F32_UNIFORM) {
+            ((double *)out)[j] = orc_f32_uniform(w[j]);
+        } else if (dtype == ORC_F64_UNIFORM) {
+            ((double *)out)[j] = orc_f64_uniform(w[2 * j], w[2 * j + 1]);
+        } else if (dtype == ORC_F32_NORMAL) {
+            double z[2];
+            orc_box_muller(w[2 * (j / 2)], w[2 * (j / 2) + 1], z);
+            ((double *)out)[j] = z[j % 2];
+        } else {
+            return -1;
+        }
+    }
+    return 0;
 }
 
 /* Number of generator words a stream of `dps` values of `dtype` consumes. */

@@ -306,9 +306,35 @@ def test_box_muller_special_cases(orc):
     assert math.isclose(z0, r_max, rel_tol=1e-15) and z1 == 0.0
     z0, z1 = orc.box_muller(0xFFFFFFFF, 12345)    # u1 = 1 -> radius 0
     assert z0 == 0.0 and z1 == 0.0
-    z0, z1 = orc.box_muller(0, 0x40000000)        # u2 = 1/4 -> pure sine
-    assert abs(z0) < 1e-15 * r_max and math.isclose(z1, r_max, rel_tol=1e-15)
+    z0, z1 = orc.box_muller(0, 0x40000000)        # u2 = 1/4 -> pure sine, cosine exactly 0
+    assert z0 == 0.0 and math.isclose(z1, r_max, rel_tol=1e-15)
+    z0, z1 = orc.box_muller(0, 0x80000000)        # u2 = 1/2 -> -r, sine exactly 0
+    assert z1 == 0.0 and math.isclose(z0, -r_max, rel_tol=1e-15)
+    z0, z1 = orc.box_muller(0, 0xC0000000)        # u2 = 3/4 -> -r on the sine
+    assert z0 == 0.0 and math.isclose(z1, -r_max, rel_tol=1e-15)
     assert r_max == pytest.approx(5.76811, abs=1e-5)
+
+
+def test_box_muller_matches_libm_away_from_quadrant_points(orc):
+    # The quadrant reduction agrees with a direct cos/sin(2 pi u2) to FP64
+    # rounding wherever the result is not near an exact zero.
+    rng = np.random.default_rng(8)
+    w = rng.integers(0, 2**32, (20000, 2), dtype=np.uint64).astype(np.uint32)
+    z = orc.box_muller_array(w[:, 0], w[:, 1])
+    u1 = ((w[:, 0] >> 8).astype(np.float64) + 1) / 2**24
+    u2 = (w[:, 1] >> 8).astype(np.float64) / 2**24
+    r = np.sqrt(-2 * np.log(u1))
+    zc, zs = r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)
+    assert np.allclose(z[:, 0], zc, rtol=1e-12, atol=1e-14) and np.allclose(z[:, 1], zs, rtol=1e-12, atol=1e-14)
+    for i in range(0, 20000, 997):
+        assert tuple(z[i]) == orc.box_muller(int(w[i, 0]), int(w[i, 1]))
+
+
+def test_map_words_matches_fill(orc):
+    for dtype in range(4):
+        n = 24
+        words = orc.stream_words(1, 77, 5, 0, orc.words_for(dtype, n))
+        assert np.array_equal(orc.map_words(dtype, words), orc.fill(1, dtype, 77, 5, 1, n))
 
 
 def test_normals_distribution(orc):
