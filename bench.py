@@ -190,6 +190,111 @@ def walk_rows(torch, orand, W, rank):
     return rows, keep
 
 
+def ragged_rows(torch, orand, W, rank):
+    """The 100,000-request ragged batch (about 30 GB of output) as one graph-launched persistent kernel."""
+    import numpy as np
+
+    recs, total = W.ragged_requests()
+    recs["seed"] += np.uint64(rank * len(recs))     # rank-disjoint request seeds
+    out = torch.empty(total, dtype=torch.uint8, device="cuda")
+    ctx = orand.default_context().handle
+    values = int(recs["length"].sum())
+    nbytes = int((recs["length"] * np.where(recs["dtype"] == 2, 8, 4).astype(np.uint64)).sum())
+
+    def run(sh):
+        orand.orand_fill_ragged(ctx, recs.ctypes.data, len(recs), out.data_ptr(), total, sh)
+
+    row = Row("ragged/batched", run, values, "values", 1, bytes_written=nbytes)
+    ty = recs["gen"] == W.TYCHE
+    row.extra = {"requests": len(recs), "GB_out": round(nbytes / 1e9, 2),
+                 "longest_tyche_values": int(recs["length"][ty].max()) if ty.any() else 0}
+    return [row], {"ragged_out": out, "recs": recs}
+
+
+def ragged_serial_baseline(torch, orand, W, n_sub=2000, reps=2):
+    """One bulk-fill launch per request (in order, one stream) vs the batcher,
+    on the first n_sub requests of the list (the full list's serial Tyche
+    chains alone take about a minute one after another)."""
+    import numpy as np
+
+    recs, _ = W.ragged_requests()
+    sub = recs[:n_sub].copy()
+    end = int(sub["out_offset_bytes"][-1] + sub["length"][-1] * 8)
+    out = torch.empty(end, dtype=torch.uint8, device="cuda")
+    ctx = orand.default_context().handle
+    sh = torch.cuda.current_stream().cuda_stream
+    res = {}
+    for name, fn in [("serial", lambda: orand.orand_fill_ragged_serial(sub.ctypes.data, len(sub), out.data_ptr(),
+                                                                        end, sh)),
+                     ("batched", lambda: orand.orand_fill_ragged(ctx, sub.ctypes.data, len(sub), out.data_ptr(),
+                                                                 end, sh))]:
+        ts = []
+        for r in range(reps + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b))
+        res[name + "_ms"] = round(statistics.mean(ts), 3)
+    res["requests"] = n_sub
+    res["values"] = int(sub["length"].sum())
+    res["batched_speedup"] = round(res["serial_ms"] / res["batched_ms"], 2)
+    return res
+
+
+def curand_reference(torch, n=1 << 28, reps=5):
+    """cuRAND's Philox4_32_10 generator on the same GPU, through its public
+    host API (device generation), for the bulk-fill sizes: GB/s per dtype."""
+    import ctypes
+
+    try:
+        lib = ctypes.CDLL("libcurand.so")
+    except OSError:
+        try:
+            lib = ctypes.CDLL("/usr/local/cuda/lib64/libcurand.so")
+        except OSError as e:
+            return {"unavailable": str(e)}
+    gen = ctypes.c_void_p()
+    if lib.curandCreateGenerator(ctypes.byref(gen), 161) != 0:
+        return {"unavailable": "curandCreateGenerator failed"}
+    lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(0x5EED))
+    lib.curandSetStream(gen, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    res = {}
+    cases = [("u32", torch.int32, lambda p: lib.curandGenerate(gen, p, ctypes.c_size_t(n))),
+             ("f32_uniform", torch.float32, lambda p: lib.curandGenerateUniform(gen, p, ctypes.c_size_t(n))),
+             ("f64_uniform", torch.float64, lambda p: lib.curandGenerateUniformDouble(gen, p, ctypes.c_size_t(n))),
+             ("f32_normal", torch.float32, lambda p: lib.curandGenerateNormal(gen, p, ctypes.c_size_t(n),
+                                                                             ctypes.c_float(0.0),
+                                                                             ctypes.c_float(1.0)))]
+    for name, dt, fn in cases:
+        buf = torch.empty(n, dtype=dt, device="cuda")
+        ptr = ctypes.c_void_p(buf.data_ptr())
+        ts = []
+        for r in range(reps + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            st = fn(ptr)
+            b.record()
+            torch.cuda.synchronize()
+            if st != 0:
+                res[name] = {"error": int(st)}
+                break
+            if r:
+                ts.append(a.elapsed_time(b))
+        if ts:
+            ms = statistics.mean(ts)
+            res[name] = {"ms": round(ms, 4), "GB/s": round(n * buf.element_size() / (ms * 1e-3) / 1e9, 1)}
+        del buf
+    lib.curandDestroyGenerator(gen)
+    torch.cuda.empty_cache()
+    return res
+
+
 def plain_walk3d_baseline(torch, orand, W, reps=2, chunk=1 << 20):
     """The plain noise-storing walk (one launch per step, z stored in forward
     and read back in backward), run over particle chunks so that the stored
@@ -233,7 +338,7 @@ def plain_walk3d_baseline(torch, orand, W, reps=2, chunk=1 << 20):
 
 # ---------------------------------------------------------------- reference --
 
-def cpu_oracle_fill_rate(threads, n_streams=1 << 21, dps=16):
+def cpu_oracle_fill_rate(threads, n_streams=1 << 24, dps=16):
     """Oracle Philox u32 fill on `threads` host threads: returns (GB/s, seconds, sample)."""
     import oracle
 
@@ -241,8 +346,8 @@ def cpu_oracle_fill_rate(threads, n_streams=1 << 21, dps=16):
     t0 = time.perf_counter()
     out = oracle.fill(0, 0, 0x5EED, 0, n_streams, dps, threads=threads)
     dt = time.perf_counter() - t0
-    return out.nbytes / dt / 1e9, dt, "philox4x32_10 u32, %d streams x %d draws (%d MiB), seed 0x5EED" % (
-        n_streams, dps, out.nbytes >> 20)
+    return out.nbytes / dt / 1e9, dt, ("philox4x32_10 u32, %d streams x %d draws (%d MiB), seed 0x5EED, "
+                                       "counter 0, on %d host threads" % (n_streams, dps, out.nbytes >> 20, threads))
 
 
 def run_reference(args, rank, world):
@@ -255,7 +360,7 @@ def run_reference(args, rank, world):
     t_total = 0.0
     sample = None
     for _ in range(args.steps):
-        v, dt, sample = cpu_oracle_fill_rate(threads, n_streams=1 << 20)
+        v, dt, sample = cpu_oracle_fill_rate(threads, n_streams=1 << 22)
         vals.append(v)
         t_total += dt
     value = statistics.mean(vals)
@@ -264,7 +369,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "philox4x32_10 u32 bulk fill, seed 0x5EED, counter 0, 16 draws per stream; "
-                               "CPU oracle on a 2^20-stream sample of the 2^24-stream workload"},
+                               "CPU oracle on a 2^22-stream sample (the first quarter) of the 2^24-stream "
+                               "workload per step"},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -300,6 +406,8 @@ def main():
     head = rows[0]  # fill/philox4x32_10/u32: the headline kernel
     wrows, _wkeep = walk_rows(torch, orand, W, rank)
     rows += wrows
+    rrows, _rkeep = ragged_rows(torch, orand, W, rank)
+    rows += rrows
     if args.only:
         rows = [r for r in rows if args.only in r.name]
         if head not in rows:
@@ -361,6 +469,7 @@ def main():
         if r.bytes_written:
             e["GB/s"] = round(world * r.bytes_written / (t * 1e-3) / 1e9, 1)
             e["frac_hbm"] = round(r.bytes_written / (t * 1e-3) / 1e9 / peak, 4)
+        e.update(getattr(r, "extra", {}))
         row_table[r.name] = e
 
     # End to end through the C ABI: the same fill, then the 1 GiB result read
@@ -389,6 +498,8 @@ def main():
         if fused:
             plain["fused_speedup"] = round(plain["ms"] / fused["ms"], 3)
         baselines["walk3d/plain_noise_storing_fwd+bwd"] = plain
+        baselines["ragged/one_launch_per_request_first2000"] = ragged_serial_baseline(torch, orand, W)
+        baselines["curand_philox4_32_10_2^28_values"] = curand_reference(torch)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -93,6 +93,18 @@ orand_status_t orand_fill_normal_f32(orand_gen_t gen, uint64_t seed, uint32_t co
 orand_status_t orand_fill(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, uint32_t counter,
                           uint64_t n_streams, uint64_t draws_per_stream, void *out, cudaStream_t stream);
 
+/* The word -> value maps alone, applied to caller-provided generator words
+ * (Fig. 1's draw helpers; BASELINE's Box-Muller): value j of `dtype` from
+ * words[j] (u32, FP32 uniform), words[2j], words[2j+1] (FP64 uniform, first
+ * high) or the pair words[2(j/2)], words[2(j/2)+1] (FP32 normal, j even the
+ * cosine, j odd the sine).  words holds 2*n_values words for FP64,
+ * 2*ceil(n_values/2) for normals, n_values otherwise; device memory, 4-byte
+ * aligned.  out: n_values elements, aligned to the element size.  Same bits
+ * as the fills produce from the same words.
+ * Errors: INVALID_ARG, OVERFLOW, ALIGNMENT, CUDA. */
+orand_status_t orand_map_words(orand_dtype_t dtype, const uint32_t *words, uint64_t n_values, void *out,
+                               cudaStream_t stream);
+
 
 /* ------------------------------------------------------------------------
  * Context: owns the library's device scratch (reduction partials, ragged

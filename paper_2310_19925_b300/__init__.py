@@ -53,6 +53,7 @@ _SIGS = {
     "orand_fill_uniform_f32": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
     "orand_fill_uniform_f64": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
     "orand_fill_normal_f32": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
+    "orand_map_words": (_i32, [_i32, _vp, _u64, _vp, _vp]),
     "orand_ctx_create": (_i32, [ctypes.POINTER(_vp)]),
     "orand_ctx_destroy": (_i32, [_vp]),
     "orand_brownian_walk": (_i32, [_vp, _vp, _vp]),
@@ -61,7 +62,22 @@ _SIGS = {
     "orand_walk3d_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_fill_ragged": (_i32, [_vp, _vp, _sz, _vp, _u64, _vp]),
+    "orand_fill_ragged_serial": (_i32, [_vp, _sz, _vp, _u64, _vp]),
+    "orand_ragged_set_config": (_i32, [_vp, _vp]),
+    "orand_ragged_get_config": (_i32, [_vp, _vp]),
+    "orand_ragged_stats": (_i32, [_vp, _vp]),
 }
+
+
+class RaggedConfig(ctypes.Structure):
+    """orand_ragged_config_t."""
+    _fields_ = [("block", _u32), ("chunk_values", _u32), ("store_bytes", _u32), ("ctas_per_sm", _u32)]
+
+
+class RaggedStats(ctypes.Structure):
+    """orand_ragged_stats_t."""
+    _fields_ = [("graph_launches", _u64), ("graph_builds", _u64), ("tune_runs", _u64), ("tuned_classes", _u64)]
 
 
 class Walk2DParams(ctypes.Structure):
@@ -168,6 +184,10 @@ def orand_fill_normal_f32(gen, seed, counter, n_streams, draws_per_stream, out_p
                                         draws_per_stream, out_ptr, stream_handle), "orand_fill_normal_f32")
 
 
+def orand_map_words(dtype, words_ptr, n_values, out_ptr, stream_handle):
+    _check(_lib().orand_map_words(dtype, words_ptr, n_values, out_ptr, stream_handle), "orand_map_words")
+
+
 # ----------------------------------------------------------- torch helpers --
 
 def torch_dtype(dtype: int):
@@ -176,6 +196,17 @@ def torch_dtype(dtype: int):
 
     return {U32: torch.int32, F32_UNIFORM: torch.float32, F64_UNIFORM: torch.float64,
             F32_NORMAL: torch.float32}[dtype]
+
+
+def map_words(dtype: int, words, n_values=None, stream=None):
+    """Apply a dtype's word->value map to a CUDA int32 tensor of words."""
+    import torch
+
+    if n_values is None:
+        n_values = words.numel() // 2 if dtype == F64_UNIFORM else words.numel()
+    out = torch.empty(n_values, dtype=torch_dtype(dtype), device=words.device)
+    orand_map_words(dtype, _ptr(words), n_values, _ptr(out) if n_values else 0, _stream_handle(stream))
+    return out
 
 
 def fill(gen: int, dtype: int, seed: int, counter: int, n_streams: int, draws_per_stream: int, out=None,
@@ -335,3 +366,58 @@ def BrownianWalk3D():
     if _BW3D is None:
         _BW3D = _autograd_function()
     return _BW3D
+
+
+# ----------------------------------------------------------------- ragged --
+
+def orand_fill_ragged(ctx, reqs_ptr, n, out_base_ptr, out_bytes, stream_handle):
+    _check(_lib().orand_fill_ragged(ctx, reqs_ptr, n, out_base_ptr, out_bytes, stream_handle), "orand_fill_ragged")
+
+
+def orand_fill_ragged_serial(reqs_ptr, n, out_base_ptr, out_bytes, stream_handle):
+    _check(_lib().orand_fill_ragged_serial(reqs_ptr, n, out_base_ptr, out_bytes, stream_handle),
+           "orand_fill_ragged_serial")
+
+
+def orand_ragged_set_config(ctx, cfg):
+    _check(_lib().orand_ragged_set_config(ctx, None if cfg is None else ctypes.byref(cfg)), "orand_ragged_set_config")
+
+
+def orand_ragged_get_config(ctx) -> RaggedConfig:
+    c = RaggedConfig()
+    _check(_lib().orand_ragged_get_config(ctx, ctypes.byref(c)), "orand_ragged_get_config")
+    return c
+
+
+def orand_ragged_stats(ctx) -> RaggedStats:
+    st = RaggedStats()
+    _check(_lib().orand_ragged_stats(ctx, ctypes.byref(st)), "orand_ragged_stats")
+    return st
+
+
+def fill_ragged(requests, out=None, out_bytes=None, serial=False, ctx=None, stream=None):
+    """Serve a ragged batch.  `requests` is a numpy array of
+    workloads.REQUEST_DTYPE records (host memory); `out` a CUDA byte buffer
+    (allocated when None, sized from the records).  serial=True uses the
+    one-launch-per-request baseline.  Returns `out`."""
+    import numpy as np
+    import torch
+
+    from .workloads import REQUEST_DTYPE, ELEM_BYTES
+
+    reqs = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
+    if out is None:
+        if out_bytes is None:
+            ends = [int(r["out_offset_bytes"]) + int(r["length"]) * ELEM_BYTES[int(r["dtype"])] for r in reqs] \
+                if len(reqs) < 4096 else (reqs["out_offset_bytes"] + reqs["length"] *
+                                          np.where(reqs["dtype"] == 2, 8, 4).astype(np.uint64)).tolist()
+            out_bytes = int(max(ends)) if len(reqs) else 0
+        out = torch.zeros(max(out_bytes, 1), dtype=torch.uint8, device="cuda")
+    nbytes = out.numel() * out.element_size() if out_bytes is None else out_bytes
+    sh = _stream_handle(stream)
+    if serial:
+        orand_fill_ragged_serial(reqs.ctypes.data, len(reqs), _ptr(out), nbytes, sh)
+    else:
+        c = (ctx or default_context()).handle
+        orand_fill_ragged(c, reqs.ctypes.data, len(reqs), _ptr(out), nbytes, sh)
+    return out

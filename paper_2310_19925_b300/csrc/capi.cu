@@ -1,6 +1,8 @@
 // Library-wide C ABI pieces: status strings, version, per-thread last CUDA
 // error, cached device properties.
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <new>
 
@@ -12,6 +14,20 @@ namespace orand_impl {
 static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
 
 void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+
+bool log_enabled()
+{
+    static const bool on = [] {
+        const char *v = getenv("ORAND_LOG");
+        return v && v[0] && v[0] != '0';
+    }();
+    return on;
+}
+
+void log_cuda_failure(const char *what, const char *file, int line, cudaError_t e)
+{
+    if (log_enabled()) fprintf(stderr, "orand: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+}
 
 namespace {
 constexpr int kMaxDevices = 64;

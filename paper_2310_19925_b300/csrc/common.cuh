@@ -24,6 +24,20 @@ inline orand_status_t cuda_status(cudaError_t e)
 // itself is asynchronous).
 inline orand_status_t launch_status() { return cuda_status(cudaGetLastError()); }
 
+// With ORAND_LOG=1 in the environment, failing CUDA calls made through
+// ORAND_CUDA_TRY are reported on stderr with their call site.
+bool log_enabled();
+void log_cuda_failure(const char *what, const char *file, int line, cudaError_t e);
+
+#define ORAND_CUDA_TRY(call)                                                            \
+    do {                                                                                \
+        cudaError_t orand_e_ = (call);                                                  \
+        if (orand_e_ != cudaSuccess) {                                                  \
+            ::orand_impl::log_cuda_failure(#call, __FILE__, __LINE__, orand_e_);        \
+            return ::orand_impl::cuda_status(orand_e_);                                 \
+        }                                                                               \
+    } while (0)
+
 struct DeviceInfo {
     int device;
     int sm_count;

@@ -9,6 +9,8 @@
 // the vectorised path consecutive threads own consecutive groups, so every
 // warp store is one fully coalesced 512-byte row; the grid is sized to the
 // resident capacity of the 148 SMs and strides over the groups.
+#include <cstdlib>
+
 #include "common.cuh"
 #include "orand_device.cuh"
 #include "values.cuh"
@@ -48,6 +50,133 @@ __global__ void __launch_bounds__(256) fill_random_access_kernel(FillArgs a)
     }
 }
 
+// ------------------------------------------------ tiled TMA-store variant
+//
+// Each thread owns a "run" of R consecutive groups of one stream (R a power
+// of two <= 8 dividing the groups per stream G), so per-stream setup (the
+// ten Philox round keys, the Threefry key schedule, the Squares key hash) is
+// paid once per R groups.  Runs are consecutive in memory, so the 256 runs
+// of a CTA form one contiguous tile of 256 * R * 16 bytes: the threads write
+// their groups into a shared-memory tile and one thread streams it to HBM
+// with a bulk asynchronous copy (cp.async.bulk, TMA engine), double-buffered
+// so the next tile is generated while the previous one drains.
+//
+// Shared-memory bank conflicts: thread x writes 16-byte slot x*R + j.  At
+// step i it handles j = (i + (x >> log2(8/R))) mod R, which puts the eight
+// threads of each 128-byte store phase on eight distinct bank groups.
+
+constexpr int kTileThreads = 256;
+
+__device__ __forceinline__ void bulk_store_s2g(void *gdst, const void *ssrc, uint32_t bytes)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+struct TileArgs {
+    uint64_t seed;
+    uint64_t n_runs;      // n_streams * G / R
+    uint64_t n_tiles;     // ceil(n_runs / 256)
+    uint64_t rps;         // runs per stream = G / R
+    int rps_shift;        // log2(rps) when rps is a power of two, else -1
+    uint32_t counter;
+    uint4 *out;           // 16-byte aligned
+};
+
+// Per-stream state of a random-access generator, set up once per run.
+template <int GEN>
+struct StreamGen;
+
+template <>
+struct StreamGen<ORAND_PHILOX4x32_10> {
+    orand::PhiloxKeys keys;
+    uint32_t counter;
+    __device__ __forceinline__ StreamGen(uint64_t key64, uint32_t c) : keys(key64), counter(c) {}
+    __device__ __forceinline__ uint4 group(uint32_t b) const { return keys.block(b, counter); }
+};
+
+template <>
+struct StreamGen<ORAND_THREEFRY4x32_20> {
+    uint4 key;
+    uint32_t counter;
+    __device__ __forceinline__ StreamGen(uint64_t key64, uint32_t c)
+        : key(make_uint4((uint32_t)key64, (uint32_t)(key64 >> 32), 0u, 0u)), counter(c) {}
+    __device__ __forceinline__ uint4 group(uint32_t b) const
+    {
+        return orand::threefry4x32_20(make_uint4(b, counter, 0u, 0u), key);
+    }
+};
+
+template <>
+struct StreamGen<ORAND_SQUARES32> {
+    uint64_t key;
+    uint32_t counter;
+    __device__ __forceinline__ StreamGen(uint64_t key64, uint32_t c) : key(orand::squares_key(key64)), counter(c) {}
+    __device__ __forceinline__ uint4 group(uint32_t b) const { return orand::squares_block(key, counter, b); }
+};
+
+template <int GEN, int DT, int R>
+__global__ void __launch_bounds__(kTileThreads) fill_tile_kernel(TileArgs a)
+{
+    extern __shared__ __align__(128) uint4 tile[];  // 2 buffers of kTileThreads * R groups
+    constexpr int ROT_SHIFT = R == 8 ? 0 : R == 4 ? 1 : R == 2 ? 2 : 3;
+    const int x = threadIdx.x;
+    int buf = 0;
+    for (uint64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        uint4 *sm = tile + buf * (kTileThreads * R);
+        // The bulk copy issued two tiles ago read this buffer; wait until it has.
+        if (x == 0) bulk_wait_read_1();
+        __syncthreads();
+        const uint64_t r = t * kTileThreads + x;
+        if (r < a.n_runs) {
+            uint64_t s, q;
+            if (a.rps_shift >= 0) {
+                s = r >> a.rps_shift;
+                q = r & (a.rps - 1);
+            } else {
+                s = r / a.rps;
+                q = r - s * a.rps;
+            }
+            if constexpr (GEN == ORAND_TYCHE) {
+                // Whole stream in one run (R == G): sequential words, slot order.
+                orand::TycheState st = orand::tyche_init(a.seed ^ s, a.counter);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    uint4 w;
+                    w.x = orand::tyche_next(st);
+                    w.y = orand::tyche_next(st);
+                    w.z = orand::tyche_next(st);
+                    w.w = orand::tyche_next(st);
+                    sm[x * R + j] = group_bits<DT>(w);
+                }
+            } else {
+                const StreamGen<GEN> sg(a.seed ^ s, a.counter);
+                const uint32_t b0 = (uint32_t)(q * R);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int j = (i + (x >> ROT_SHIFT)) & (R - 1);
+                    sm[x * R + j] = group_bits<DT>(sg.group(b0 + (uint32_t)j));
+                }
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (x == 0) {
+            const uint64_t r0 = t * kTileThreads;
+            const uint64_t runs = min((uint64_t)kTileThreads, a.n_runs - r0);
+            bulk_store_s2g(a.out + r0 * R, sm, (uint32_t)(runs * R * 16));
+            bulk_commit();
+        }
+        buf ^= 1;
+    }
+    if (x == 0) bulk_wait_all();
+}
+
 // Tyche is sequential within a stream: one thread walks one whole stream.
 template <int DT, bool VEC>
 __global__ void __launch_bounds__(256) fill_tyche_kernel(FillArgs a)
@@ -63,6 +192,50 @@ __global__ void __launch_bounds__(256) fill_tyche_kernel(FillArgs a)
             w.w = orand::tyche_next(st);
             store_group<DT, VEC>(a.out, s * a.G + b, s, b, a.dps, w);
         }
+    }
+}
+
+template <int GEN, int DT, int R>
+static orand_status_t launch_tile_r(const TileArgs &a, const DeviceInfo &info, cudaStream_t stream)
+{
+    const size_t smem = 2u * kTileThreads * R * sizeof(uint4);
+    static bool configured = false;  // per instantiation; idempotent, so a race is harmless
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(fill_tile_kernel<GEN, DT, R>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_status(e);
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_tile_kernel<GEN, DT, R>,
+                                                                  kTileThreads, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = (uint64_t)per_sm * info.sm_count;
+    if (grid > a.n_tiles) grid = a.n_tiles;
+    fill_tile_kernel<GEN, DT, R><<<(unsigned)grid, kTileThreads, smem, stream>>>(a);
+    return launch_status();
+}
+
+template <int GEN, int DT>
+static orand_status_t launch_tile_dt(int R, const TileArgs &a, const DeviceInfo &info, cudaStream_t stream)
+{
+    switch (R) {
+    case 8: return launch_tile_r<GEN, DT, 8>(a, info, stream);
+    case 4: return launch_tile_r<GEN, DT, 4>(a, info, stream);
+    case 2: return launch_tile_r<GEN, DT, 2>(a, info, stream);
+    default: return launch_tile_r<GEN, DT, 1>(a, info, stream);
+    }
+}
+
+template <int GEN>
+static orand_status_t launch_tile_gen(int dt, int R, const TileArgs &a, const DeviceInfo &info, cudaStream_t stream)
+{
+    switch (dt) {
+    case ORAND_U32: return launch_tile_dt<GEN, ORAND_U32>(R, a, info, stream);
+    case ORAND_F32_UNIFORM: return launch_tile_dt<GEN, ORAND_F32_UNIFORM>(R, a, info, stream);
+    case ORAND_F64_UNIFORM: return launch_tile_dt<GEN, ORAND_F64_UNIFORM>(R, a, info, stream);
+    default: return launch_tile_dt<GEN, ORAND_F32_NORMAL>(R, a, info, stream);
     }
 }
 
@@ -118,6 +291,16 @@ orand_status_t fill_validate(int gen, int dt, uint64_t n_streams, uint64_t dps, 
     return ORAND_OK;
 }
 
+// ORAND_FILL_TILE=0 selects the untiled kernels (for comparison runs).
+static bool tile_path_disabled()
+{
+    static const bool off = [] {
+        const char *v = getenv("ORAND_FILL_TILE");
+        return v && v[0] == '0';
+    }();
+    return off;
+}
+
 orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uint64_t n_streams, uint64_t dps,
                            void *out, cudaStream_t stream)
 {
@@ -128,6 +311,30 @@ orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uin
     if ((st = current_device(&info)) != ORAND_OK) return st;
 
     const uint32_t V = dt == ORAND_F64_UNIFORM ? 2u : 4u;
+    const uint64_t G = ceil_div(dps, V);
+    const bool vec16 = (dps % V == 0) && ((uintptr_t)out % 16 == 0);
+    // Tiled path: vector-aligned output; Tyche only when a whole stream fits a run.
+    if (vec16 && !(gen == ORAND_TYCHE && G > 8) && !tile_path_disabled()) {
+        int R = 1;
+        if (gen == ORAND_TYCHE) R = (int)G;
+        else while (R < 8 && G % (2 * R) == 0) R *= 2;
+        if (gen != ORAND_TYCHE || R == 1 || R == 2 || R == 4 || R == 8) {
+            TileArgs t;
+            t.seed = seed;
+            t.counter = counter;
+            t.rps = G / R;
+            t.n_runs = n_streams * t.rps;
+            t.n_tiles = ceil_div(t.n_runs, kTileThreads);
+            t.rps_shift = (t.rps & (t.rps - 1)) == 0 ? __builtin_ctzll(t.rps) : -1;
+            t.out = (uint4 *)out;
+            switch (gen) {
+            case ORAND_PHILOX4x32_10: return launch_tile_gen<ORAND_PHILOX4x32_10>(dt, R, t, info, stream);
+            case ORAND_THREEFRY4x32_20: return launch_tile_gen<ORAND_THREEFRY4x32_20>(dt, R, t, info, stream);
+            case ORAND_SQUARES32: return launch_tile_gen<ORAND_SQUARES32>(dt, R, t, info, stream);
+            default: return launch_tile_gen<ORAND_TYCHE>(dt, R, t, info, stream);
+            }
+        }
+    }
     FillArgs a;
     a.seed = seed;
     a.counter = counter;
@@ -152,9 +359,66 @@ orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uin
     return launch_status();
 }
 
+// Word -> value map over caller words: group g reads words 4g..4g+3 (the
+// missing tail words of the last group read as 0; their values are not
+// stored) and writes its values masked to j < n_values.
+template <int DT>
+__global__ void __launch_bounds__(256) map_words_kernel(const uint32_t *__restrict__ w, uint64_t n_words,
+                                                        uint64_t n_values, char *__restrict__ out)
+{
+    constexpr uint32_t V = Vals<DT>::V;
+    constexpr uint32_t E = DT == ORAND_F64_UNIFORM ? 8u : 4u;
+    const uint64_t n_groups = (n_values + V - 1) / V;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_groups;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = (4 * g + i < n_words) ? w[4 * g + i] : 0u;
+        const uint4 bits = group_bits<DT>(make_uint4(v[0], v[1], v[2], v[3]));
+        store_bits_masked<DT>(out + g * V * E, g * V, n_values, bits);
+    }
+}
+
+orand_status_t map_words_launch(int dt, const uint32_t *words, uint64_t n_values, void *out, cudaStream_t stream)
+{
+    if (dt < 0 || dt > 3) return ORAND_ERR_INVALID_ARG;
+    uint64_t n_words = 0, bytes = 0;
+    if (!stream_words(dt, n_values, &n_words)) return ORAND_ERR_OVERFLOW;
+    const uint64_t elem = dt == ORAND_F64_UNIFORM ? 8 : 4;
+    if (mul_overflows(n_values, elem, &bytes)) return ORAND_ERR_OVERFLOW;
+    if (n_values == 0) return ORAND_OK;
+    if (words == nullptr || out == nullptr) return ORAND_ERR_INVALID_ARG;
+    if ((uintptr_t)words % 4 || (uintptr_t)out % elem) return ORAND_ERR_ALIGNMENT;
+    DeviceInfo info;
+    orand_status_t st = current_device(&info);
+    if (st != ORAND_OK) return st;
+    const uint64_t groups = ceil_div(n_values, dt == ORAND_F64_UNIFORM ? 2 : 4);
+    const unsigned grid = grid_for(groups, 256, info.sm_count, info.max_threads_per_sm / 256);
+    switch (dt) {
+    case ORAND_U32: map_words_kernel<ORAND_U32><<<grid, 256, 0, stream>>>(words, n_words, n_values, (char *)out); break;
+    case ORAND_F32_UNIFORM:
+        map_words_kernel<ORAND_F32_UNIFORM><<<grid, 256, 0, stream>>>(words, n_words, n_values, (char *)out);
+        break;
+    case ORAND_F64_UNIFORM:
+        map_words_kernel<ORAND_F64_UNIFORM><<<grid, 256, 0, stream>>>(words, n_words, n_values, (char *)out);
+        break;
+    default:
+        map_words_kernel<ORAND_F32_NORMAL><<<grid, 256, 0, stream>>>(words, n_words, n_values, (char *)out);
+        break;
+    }
+    return launch_status();
+}
+
 }  // namespace orand_impl
 
 extern "C" {
+
+orand_status_t orand_map_words(orand_dtype_t dtype, const uint32_t *words, uint64_t n_values, void *out,
+                               cudaStream_t stream)
+{
+    return orand_impl::map_words_launch((int)dtype, words, n_values, out, stream);
+}
+
 
 orand_status_t orand_fill(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, uint32_t counter,
                           uint64_t n_streams, uint64_t draws_per_stream, void *out, cudaStream_t stream)

@@ -5,9 +5,9 @@
 //
 // Scheduling (host, O(n log n)):
 //   * Tyche is sequential within a stream, so each Tyche request is one
-//     lane's serial chain.  Requests are sorted longest first (LPT) and taken
-//     32 at a time by warps, so the longest chains start first and warps see
-//     similar lengths.
+//     lane's serial chain.  Requests of one dtype are sorted longest first and
+//     grouped 32 to a warp item; items of all dtypes are merged longest first
+//     (LPT), so the longest chains start first and a warp runs one code path.
 //   * The random-access generators (Philox, Threefry, Squares) are cut into
 //     chunks of `chunk_values` values.  A warp takes one chunk at a time; its
 //     32 lanes write consecutive 16-byte groups, and per-stream setup (round
@@ -43,17 +43,18 @@ struct RaggedReq {
 };
 static_assert(sizeof(RaggedReq) == 40, "RaggedReq layout");
 
-struct RaggedArgs {
-    const RaggedReq *reqs;
-    const uint32_t *item_req;     // request index of each chunk item
-    const uint32_t *tyche_order;  // Tyche request indices, longest first
-    unsigned long long *cursors;  // [0] Tyche warp items, [1] chunk items
+// Header at the start of the device table: everything that changes from one
+// batch to the next, so the captured graph (copy + kernel) does not.
+struct RaggedHeader {
+    char *out;
     uint64_t n_items;
     uint64_t chunk_values;
-    uint32_t n_ty;
-    uint32_t n_ty_items;
-    char *out;
+    uint64_t off_reqs, off_items, off_tyche, off_cursors;  // bytes from the table start
+    uint32_t n_ty_items;                                   // Tyche warp items (32 slots each)
+    uint32_t pad;
 };
+static_assert(sizeof(RaggedHeader) <= 256, "header slot");
+constexpr uint32_t kNoRequest = 0xFFFFFFFFu;
 
 // 16-byte store of one group's bits as SW-byte stores (dst 16-byte aligned).
 template <int SW>
@@ -82,32 +83,53 @@ __device__ __forceinline__ void store_req_group(char *base, bool vec, uint64_t g
     else store_bits_masked<DT>(base + j0 * E, j0, L, v);
 }
 
-template <int SW>
-__device__ __forceinline__ void store_req_group_rt(int dt, char *base, bool vec, uint64_t g, uint64_t L, uint4 w)
+__device__ __forceinline__ uint4 tyche_next4(orand::TycheState &st)
 {
-    switch (dt) {
-    case ORAND_U32: store_req_group<ORAND_U32, SW>(base, vec, g, L, w); break;
-    case ORAND_F32_UNIFORM: store_req_group<ORAND_F32_UNIFORM, SW>(base, vec, g, L, w); break;
-    case ORAND_F64_UNIFORM: store_req_group<ORAND_F64_UNIFORM, SW>(base, vec, g, L, w); break;
-    default: store_req_group<ORAND_F32_NORMAL, SW>(base, vec, g, L, w); break;
-    }
+    uint4 w;
+    w.x = orand::tyche_next(st);
+    w.y = orand::tyche_next(st);
+    w.z = orand::tyche_next(st);
+    w.w = orand::tyche_next(st);
+    return w;
 }
 
-// One lane serves one whole Tyche request.
-template <int SW>
+// One lane serves one whole Tyche request.  The MIX chain is the critical
+// path, so the next group's words are generated before the current group is
+// converted and stored: the two are independent and the scheduler overlaps
+// them.
+template <int DT, int SW>
 __device__ __forceinline__ void tyche_request(const RaggedReq &q, char *out)
 {
+    constexpr uint64_t V = Vals<DT>::V;
+    constexpr uint64_t E = DT == ORAND_F64_UNIFORM ? 8u : 4u;
     char *base = out + q.out_off;
-    const uint64_t V = q.dtype == ORAND_F64_UNIFORM ? 2u : 4u;
-    const uint64_t G = (q.length + V - 1) / V;
+    const uint64_t L = q.length, full = L / V;
     orand::TycheState st = orand::tyche_init(q.seed, q.counter);
-    for (uint64_t g = 0; g < G; ++g) {
-        uint4 w;
-        w.x = orand::tyche_next(st);
-        w.y = orand::tyche_next(st);
-        w.z = orand::tyche_next(st);
-        w.w = orand::tyche_next(st);
-        store_req_group_rt<SW>(q.dtype, base, q.vec, g, q.length, w);
+    uint4 w = tyche_next4(st);
+    if (q.vec) {
+        for (uint64_t g = 0; g < full; ++g) {
+            const uint4 cur = w;
+            w = tyche_next4(st);
+            store16<SW>(base + g * V * E, group_bits<DT>(cur));
+        }
+    } else {
+        for (uint64_t g = 0; g < full; ++g) {
+            const uint4 cur = w;
+            w = tyche_next4(st);
+            store_bits_masked<DT>(base + g * V * E, g * V, L, group_bits<DT>(cur));
+        }
+    }
+    if (full * V < L) store_bits_masked<DT>(base + full * V * E, full * V, L, group_bits<DT>(w));
+}
+
+template <int SW>
+__device__ __forceinline__ void tyche_request_rt(const RaggedReq &q, char *out)
+{
+    switch (q.dtype) {
+    case ORAND_U32: tyche_request<ORAND_U32, SW>(q, out); break;
+    case ORAND_F32_UNIFORM: tyche_request<ORAND_F32_UNIFORM, SW>(q, out); break;
+    case ORAND_F64_UNIFORM: tyche_request<ORAND_F64_UNIFORM, SW>(q, out); break;
+    default: tyche_request<ORAND_F32_NORMAL, SW>(q, out); break;
     }
 }
 
@@ -144,36 +166,38 @@ __device__ __forceinline__ void chunk_dt(const RaggedReq &q, char *out, uint64_t
 }
 
 template <int SW>
-__global__ void ragged_kernel(RaggedArgs a)
+__global__ void ragged_kernel(char *table)
 {
+    const RaggedHeader h = *reinterpret_cast<const RaggedHeader *>(table);
+    const RaggedReq *reqs = reinterpret_cast<const RaggedReq *>(table + h.off_reqs);
+    const uint32_t *item_req = reinterpret_cast<const uint32_t *>(table + h.off_items);
+    const uint32_t *tyche = reinterpret_cast<const uint32_t *>(table + h.off_tyche);
+    unsigned long long *cursors = reinterpret_cast<unsigned long long *>(table + h.off_cursors);
     const int lane = threadIdx.x & 31;
-    // Phase 1: Tyche requests, 32 per warp item, longest first.
+    // Phase 1: Tyche warp items (32 requests of one dtype), longest first.
     for (;;) {
         unsigned long long wi = 0;
-        if (lane == 0) wi = atomicAdd(&a.cursors[0], 1ull);
+        if (lane == 0) wi = atomicAdd(&cursors[0], 1ull);
         wi = __shfl_sync(0xFFFFFFFFu, wi, 0);
-        if (wi >= a.n_ty_items) break;
-        const uint64_t k = wi * 32 + lane;
-        if (k < a.n_ty) {
-            const RaggedReq q = a.reqs[a.tyche_order[k]];
-            tyche_request<SW>(q, a.out);
-        }
+        if (wi >= h.n_ty_items) break;
+        const uint32_t r = tyche[wi * 32 + lane];
+        if (r != kNoRequest) tyche_request_rt<SW>(reqs[r], h.out);
     }
     // Phase 2: chunks of the random-access requests.
     for (;;) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(&a.cursors[1], 1ull);
+        if (lane == 0) item = atomicAdd(&cursors[1], 1ull);
         item = __shfl_sync(0xFFFFFFFFu, item, 0);
-        if (item >= a.n_items) break;
-        const RaggedReq q = a.reqs[a.item_req[item]];
+        if (item >= h.n_items) break;
+        const RaggedReq q = reqs[item_req[item]];
         const uint64_t V = q.dtype == ORAND_F64_UNIFORM ? 2u : 4u;
-        const uint64_t v0 = (item - q.first_item) * a.chunk_values;
-        const uint64_t v1 = min(q.length, v0 + a.chunk_values);
+        const uint64_t v0 = (item - q.first_item) * h.chunk_values;
+        const uint64_t v1 = min(q.length, v0 + h.chunk_values);
         const uint64_t g0 = v0 / V, g1 = (v1 + V - 1) / V;
         switch (q.gen) {
-        case ORAND_PHILOX4x32_10: chunk_dt<ORAND_PHILOX4x32_10, SW>(q, a.out, g0, g1, lane); break;
-        case ORAND_THREEFRY4x32_20: chunk_dt<ORAND_THREEFRY4x32_20, SW>(q, a.out, g0, g1, lane); break;
-        default: chunk_dt<ORAND_SQUARES32, SW>(q, a.out, g0, g1, lane); break;
+        case ORAND_PHILOX4x32_10: chunk_dt<ORAND_PHILOX4x32_10, SW>(q, h.out, g0, g1, lane); break;
+        case ORAND_THREEFRY4x32_20: chunk_dt<ORAND_THREEFRY4x32_20, SW>(q, h.out, g0, g1, lane); break;
+        default: chunk_dt<ORAND_SQUARES32, SW>(q, h.out, g0, g1, lane); break;
         }
     }
 }
@@ -189,15 +213,13 @@ struct RaggedConfig {
 
 struct GraphKey {
     RaggedConfig cfg;
-    uint64_t n_items, table_bytes;
-    uint32_t n_ty, n;
-    char *out;
-    cudaStream_t unused;
+    uint64_t copy_bytes;
+    void *d_tables, *h_staging;
     bool operator==(const GraphKey &o) const
     {
         return cfg.block == o.cfg.block && cfg.chunk_values == o.cfg.chunk_values &&
                cfg.store_bytes == o.cfg.store_bytes && cfg.ctas_per_sm == o.cfg.ctas_per_sm &&
-               n_items == o.n_items && table_bytes == o.table_bytes && n_ty == o.n_ty && n == o.n && out == o.out;
+               copy_bytes == o.copy_bytes && d_tables == o.d_tables && h_staging == o.h_staging;
     }
 };
 
@@ -244,10 +266,11 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 struct Plan {
     uint64_t chunk_values = 0;
     std::vector<RaggedReq> reqs;
-    std::vector<uint32_t> tyche;
+    std::vector<uint32_t> tyche;  // warp items of 32 slots, kNoRequest-padded
+    uint64_t n_tyche = 0;
     uint64_t n_items = 0;
     uint64_t total_values = 0;
-    size_t off_items = 0, off_tyche = 0, off_cursors = 0, table_bytes = 0;
+    size_t off_reqs = 256, off_items = 0, off_tyche = 0, off_cursors = 0, table_bytes = 0;
 };
 
 static uint64_t words_for(uint32_t dt, uint64_t len)
@@ -264,6 +287,8 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
     p->chunk_values = chunk_values;
     p->reqs.resize(n);
     p->tyche.clear();
+    p->n_tyche = 0;
+    std::vector<uint32_t> ty[4];
     p->n_items = 0;
     p->total_values = 0;
     std::vector<std::pair<uint64_t, uint64_t>> ranges;
@@ -290,8 +315,8 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
         p->total_values += q.length;
         if (q.length == 0) continue;
         if (q.gen == ORAND_TYCHE) {
-            if (p->tyche.size() >= 0xFFFFFFFFull) return ORAND_ERR_OVERFLOW;
-            p->tyche.push_back((uint32_t)i);
+            ty[q.dtype].push_back((uint32_t)i);
+            ++p->n_tyche;
         } else {
             p->n_items += (q.length + chunk_values - 1) / chunk_values;
         }
@@ -302,21 +327,50 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
         for (size_t i = 1; i < ranges.size(); ++i)
             if (ranges[i].first < ranges[i - 1].second) return ORAND_ERR_INVALID_ARG;
     }
-    // Longest Tyche chains first; ties by request index keep the plan deterministic.
-    std::sort(p->tyche.begin(), p->tyche.end(), [&](uint32_t a, uint32_t b) {
-        if (p->reqs[a].length != p->reqs[b].length) return p->reqs[a].length > p->reqs[b].length;
-        return a < b;
-    });
-    p->off_items = align_up(n * sizeof(RaggedReq), 256);
+    // Tyche warp items: 32 requests of one dtype (so a warp runs one code
+    // path), longest chains first within each dtype, and the items of all
+    // dtypes merged longest-first (LPT).  Ties by request index keep the plan
+    // deterministic.
+    struct WarpItem {
+        uint64_t longest;
+        uint32_t dtype, first;
+    };
+    std::vector<WarpItem> items;
+    for (uint32_t d = 0; d < 4; ++d) {
+        std::sort(ty[d].begin(), ty[d].end(), [&](uint32_t a, uint32_t b) {
+            if (p->reqs[a].length != p->reqs[b].length) return p->reqs[a].length > p->reqs[b].length;
+            return a < b;
+        });
+        for (uint32_t k = 0; k < ty[d].size(); k += 32) items.push_back({p->reqs[ty[d][k]].length, d, k});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const WarpItem &a, const WarpItem &b) { return a.longest > b.longest; });
+    p->tyche.assign(items.size() * 32, kNoRequest);
+    for (size_t w = 0; w < items.size(); ++w)
+        for (uint32_t l = 0; l < 32 && items[w].first + l < ty[items[w].dtype].size(); ++l)
+            p->tyche[w * 32 + l] = ty[items[w].dtype][items[w].first + l];
+    p->off_reqs = 256;
+    p->off_items = align_up(p->off_reqs + n * sizeof(RaggedReq), 256);
     p->off_tyche = align_up(p->off_items + p->n_items * sizeof(uint32_t), 256);
     p->off_cursors = align_up(p->off_tyche + p->tyche.size() * sizeof(uint32_t), 256);
     p->table_bytes = p->off_cursors + 256;
     return ORAND_OK;
 }
 
-static void write_staging(const Plan &p, char *h)
+static void write_staging(const Plan &p, char *out, char *h)
 {
-    std::memcpy(h, p.reqs.data(), p.reqs.size() * sizeof(RaggedReq));
+    RaggedHeader hd{};
+    hd.out = out;
+    hd.n_items = p.n_items;
+    hd.chunk_values = p.chunk_values;
+    hd.off_reqs = p.off_reqs;
+    hd.off_items = p.off_items;
+    hd.off_tyche = p.off_tyche;
+    hd.off_cursors = p.off_cursors;
+    hd.n_ty_items = (uint32_t)(p.tyche.size() / 32);
+    std::memset(h, 0, 256);
+    std::memcpy(h, &hd, sizeof(hd));
+    std::memcpy(h + p.off_reqs, p.reqs.data(), p.reqs.size() * sizeof(RaggedReq));
     uint32_t *items = (uint32_t *)(h + p.off_items);
     uint64_t k = 0;
     for (size_t i = 0; i < p.reqs.size(); ++i) {
@@ -327,6 +381,15 @@ static void write_staging(const Plan &p, char *h)
     }
     std::memcpy(h + p.off_tyche, p.tyche.data(), p.tyche.size() * sizeof(uint32_t));
     std::memset(h + p.off_cursors, 0, 256);
+}
+
+// Bytes the graph copies: the table rounded up to a power of two, so batches
+// of similar size reuse one graph.
+static size_t copy_bucket(size_t table_bytes)
+{
+    size_t b = 1 << 16;
+    while (b < table_bytes) b <<= 1;
+    return b;
 }
 
 static orand_status_t ensure_buffers(RaggedState *s, size_t bytes)
@@ -371,23 +434,9 @@ static orand_status_t ensure_buffers(RaggedState *s, size_t bytes)
     return ORAND_OK;
 }
 
-static RaggedArgs make_args(const RaggedState *s, const Plan &p, const RaggedConfig &c, char *out)
-{
-    RaggedArgs a;
-    char *d = (char *)s->d_tables;
-    a.reqs = (const RaggedReq *)d;
-    a.item_req = (const uint32_t *)(d + p.off_items);
-    a.tyche_order = (const uint32_t *)(d + p.off_tyche);
-    a.cursors = (unsigned long long *)(d + p.off_cursors);
-    a.n_items = p.n_items;
-    a.chunk_values = c.chunk_values;
-    a.n_ty = (uint32_t)p.tyche.size();
-    a.n_ty_items = (uint32_t)((p.tyche.size() + 31) / 32);
-    a.out = out;
-    return a;
-}
-
-static orand_status_t launch_kernel(const RaggedArgs &a, const RaggedConfig &c, cudaStream_t stream)
+// Persistent grid for a configuration: as many CTAs as fit on every SM (or
+// the configured cap).  Queried outside any stream capture.
+static orand_status_t ragged_grid(const RaggedConfig &c, unsigned *grid)
 {
     DeviceInfo info;
     orand_status_t st = current_device(&info);
@@ -395,15 +444,18 @@ static orand_status_t launch_kernel(const RaggedArgs &a, const RaggedConfig &c, 
     const void *fn = c.store_bytes == 16 ? (const void *)ragged_kernel<16>
                      : c.store_bytes == 8 ? (const void *)ragged_kernel<8> : (const void *)ragged_kernel<4>;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)c.block, 0);
-    if (e != cudaSuccess) return cuda_status(e);
+    ORAND_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)c.block, 0));
     if (per_sm < 1) per_sm = 1;
     if (c.ctas_per_sm && (int)c.ctas_per_sm < per_sm) per_sm = (int)c.ctas_per_sm;
-    const unsigned grid = (unsigned)(per_sm * info.sm_count);
-    if (c.store_bytes == 16) ragged_kernel<16><<<grid, c.block, 0, stream>>>(a);
-    else if (c.store_bytes == 8) ragged_kernel<8><<<grid, c.block, 0, stream>>>(a);
-    else ragged_kernel<4><<<grid, c.block, 0, stream>>>(a);
-    return launch_status();
+    *grid = (unsigned)(per_sm * info.sm_count);
+    return ORAND_OK;
+}
+
+static void launch_kernel(char *table, const RaggedConfig &c, unsigned grid, cudaStream_t stream)
+{
+    if (c.store_bytes == 16) ragged_kernel<16><<<grid, c.block, 0, stream>>>(table);
+    else if (c.store_bytes == 8) ragged_kernel<8><<<grid, c.block, 0, stream>>>(table);
+    else ragged_kernel<4><<<grid, c.block, 0, stream>>>(table);
 }
 
 static bool valid_config(const RaggedConfig &c)
@@ -435,9 +487,9 @@ static orand_status_t autotune(RaggedState *s, const orand_request_t *r, size_t 
     for (uint32_t ch : chunks) {
         Plan p;
         if ((st = plan_requests(r, n, out, out_bytes, ch, &p, false)) != ORAND_OK) break;
-        if ((st = ensure_buffers(s, p.table_bytes)) != ORAND_OK) break;
+        if ((st = ensure_buffers(s, copy_bucket(p.table_bytes))) != ORAND_OK) break;
         cudaEventSynchronize(s->staging_free);
-        write_staging(p, (char *)s->h_staging);
+        write_staging(p, out, (char *)s->h_staging);
         cudaError_t e = cudaMemcpyAsync(s->d_tables, s->h_staging, p.table_bytes, cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess) { st = cuda_status(e); break; }
         for (uint32_t bl : blocks) {
@@ -446,10 +498,12 @@ static orand_status_t autotune(RaggedState *s, const orand_request_t *r, size_t 
                 cand.chunk_values = ch;
                 cand.store_bytes = sw;
                 cand.ctas_per_sm = 0;
-                const RaggedArgs args = make_args(s, p, cand, out);
-                cudaMemsetAsync(args.cursors, 0, 16, stream);
+                unsigned grid = 0;
+                if ((st = ragged_grid(cand, &grid)) != ORAND_OK) break;
+                cudaMemsetAsync((char *)s->d_tables + p.off_cursors, 0, 16, stream);
                 cudaEventRecord(a, stream);
-                if ((st = launch_kernel(args, cand, stream)) != ORAND_OK) break;
+                launch_kernel((char *)s->d_tables, cand, grid, stream);
+                if ((st = launch_status()) != ORAND_OK) break;
                 cudaEventRecord(b, stream);
                 e = cudaEventSynchronize(b);
                 if (e != cudaSuccess) { st = cuda_status(e); break; }
@@ -508,50 +562,55 @@ orand_status_t ragged_serve(orand_ctx_t ctx, const orand_request_t *reqs, size_t
     if (cfg.chunk_values != plan.chunk_values &&
         (st = plan_requests(reqs, n, out, out_bytes, cfg.chunk_values, &plan, false)) != ORAND_OK)
         return st;
-    if ((st = ensure_buffers(s, plan.table_bytes)) != ORAND_OK) return st;
+    const size_t copy_bytes = copy_bucket(plan.table_bytes);
+    if ((st = ensure_buffers(s, copy_bytes)) != ORAND_OK) return st;
 
     // The previous batch's graph must have copied the staging buffer out
     // before it is rewritten.
-    cudaError_t e = cudaEventSynchronize(s->staging_free);
-    if (e != cudaSuccess) return cuda_status(e);
-    write_staging(plan, (char *)s->h_staging);
+    cudaError_t e = cudaSuccess;
+    ORAND_CUDA_TRY(cudaEventSynchronize(s->staging_free));
+    write_staging(plan, out, (char *)s->h_staging);
 
     GraphKey key{};
     key.cfg = cfg;
-    key.n_items = plan.n_items;
-    key.table_bytes = plan.table_bytes;
-    key.n_ty = (uint32_t)plan.tyche.size();
-    key.n = (uint32_t)n;
-    key.out = out;
+    key.copy_bytes = copy_bytes;
+    key.d_tables = s->d_tables;
+    key.h_staging = s->h_staging;
     if (!s->have_graph || !(key == s->key)) {
         if (s->exec) {
             cudaGraphExecDestroy(s->exec);
             s->exec = nullptr;
         }
         s->have_graph = false;
-        const RaggedArgs args = make_args(s, plan, cfg, out);
+        unsigned grid = 0;
+        if ((st = ragged_grid(cfg, &grid)) != ORAND_OK) return st;
         cudaStream_t cs = s->capture_stream;
-        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_status(e);
-        cudaMemcpyAsync(s->d_tables, s->h_staging, plan.table_bytes, cudaMemcpyHostToDevice, cs);
-        cudaEventRecord(s->staging_free, cs);
-        const orand_status_t lst = launch_kernel(args, cfg, cs);
+        ORAND_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        // Captured: table copy, an external event record (the host waits on it
+        // before rewriting the staging buffer), the persistent kernel.
+        cudaMemcpyAsync(s->d_tables, s->h_staging, copy_bytes, cudaMemcpyHostToDevice, cs);
+        cudaEventRecordWithFlags(s->staging_free, cs, cudaEventRecordExternal);
+        launch_kernel((char *)s->d_tables, cfg, grid, cs);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cs, &graph);
-        if (lst != ORAND_OK) {
+        if (e != cudaSuccess) {
+            log_cuda_failure("cudaStreamEndCapture", __FILE__, __LINE__, e);
             if (graph) cudaGraphDestroy(graph);
-            return lst;
+            return cuda_status(e);
         }
-        if (e != cudaSuccess) return cuda_status(e);
         e = cudaGraphInstantiate(&s->exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_status(e);
+        if (e != cudaSuccess) {
+            log_cuda_failure("cudaGraphInstantiate", __FILE__, __LINE__, e);
+            return cuda_status(e);
+        }
         s->key = key;
         s->have_graph = true;
         ++s->graph_builds;
     }
-    if (s->batch_pending && (e = cudaStreamWaitEvent(stream, s->batch_done, 0)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaGraphLaunch(s->exec, stream)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaEventRecord(s->batch_done, stream)) != cudaSuccess) return cuda_status(e);
+    if (s->batch_pending) ORAND_CUDA_TRY(cudaStreamWaitEvent(stream, s->batch_done, 0));
+    ORAND_CUDA_TRY(cudaGraphLaunch(s->exec, stream));
+    ORAND_CUDA_TRY(cudaEventRecord(s->batch_done, stream));
     s->batch_pending = true;
     s->last_cfg = cfg;
     ++s->graph_launches;

@@ -39,7 +39,7 @@ RAGGED = dict(n_requests=100_000, max_log2_len=20, list_seed=20231030)
 
 # Layout of one ragged request record (matches the C struct orand_request_t).
 REQUEST_DTYPE = np.dtype([
-    ("gen", "<u4"), ("dtype", "<u4"), ("seed", "<u8"), ("counter", "<u4"), ("_pad", "<u4"),
+    ("gen", "<u4"), ("dtype", "<u4"), ("seed", "<u8"), ("counter", "<u4"), ("reserved", "<u4"),
     ("length", "<u8"), ("out_offset_bytes", "<u8"),
 ])
 assert REQUEST_DTYPE.itemsize == 40

@@ -103,3 +103,32 @@ def test_context_needs_a_device_or_succeeds(lib):
         assert st in (-5, -7) and not h.value
     assert lib.orand_ctx_create(None) == -1
     assert lib.orand_ctx_destroy(None) == -1
+
+
+def _reqs(rows):
+    import numpy as np
+
+    from paper_2310_19925_b300.workloads import REQUEST_DTYPE
+
+    a = np.zeros(len(rows), REQUEST_DTYPE)
+    for i, r in enumerate(rows):
+        for k, v in r.items():
+            a[i][k] = v
+    return a
+
+
+def test_ragged_arguments_rejected_on_host(lib):
+    ok = dict(gen=0, dtype=0, seed=1, counter=2, length=8, out_offset_bytes=0)
+    serial = lib.orand_fill_ragged_serial
+    r = _reqs([ok])
+    assert serial(r.ctypes.data, 0, None, 0, None) == 0                                  # empty batch
+    assert serial(None, 3, 16, 64, None) == -1
+    for bad, code in [(dict(ok, gen=4), -1), (dict(ok, dtype=9), -1), (dict(ok, reserved=1), -1),
+                      (dict(ok, length=2**32 + 1), -2), (dict(ok, dtype=2, length=2**31 + 1), -2),
+                      (dict(ok, out_offset_bytes=232), -2), (dict(ok, out_offset_bytes=2**64 - 8), -2),
+                      (dict(ok, out_offset_bytes=2), -3), (dict(ok, dtype=2, out_offset_bytes=4), -3)]:
+        rr = _reqs([ok, bad])
+        assert serial(rr.ctypes.data, 2, 16, 256, None) == code, bad
+    assert lib.orand_fill_ragged(None, r.ctypes.data, 1, 16, 64, None) == -1            # no context
+    cfg = orand.RaggedConfig(256, 8192, 16, 0)
+    assert lib.orand_ragged_set_config(None, ctypes.byref(cfg)) == -1

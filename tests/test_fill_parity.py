@@ -53,7 +53,7 @@ def gpu_fill(torch, gen, dtype, seed, counter, n_streams, dps, offset_elems=0):
     return to_numpy(out)
 
 
-SHAPES = [(1, 1), (3, 5), (257, 4), (100, 16), (33, 67), (1000, 8), (5, 130)]
+SHAPES = [(1, 1), (3, 5), (257, 4), (100, 16), (33, 67), (1000, 8), (5, 130), (77, 96), (300, 48), (513, 32)]
 
 
 @pytest.mark.parametrize("gen", GENS)

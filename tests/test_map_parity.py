@@ -1,0 +1,103 @@
+"""Exhaustive GPU checks of the word -> value maps against the oracle.
+
+The Box-Muller map is checked on every possible input of each half:
+  * all 2^24 values of u1 with u2 = 0, so z0 is the radius alone and z1 is 0;
+  * all 2^24 values of u2 at one fixed radius (this includes the exact zeros
+    at u2 = 0, 1/4, 1/2, 3/4);
+  * 2^24 random word pairs.
+The bar for normals is 4 ulp (ordered-integer distance to the FP64 value
+rounded to FP32).  The components are held to 2 ulp.  The uniform maps are
+bit-exact: the FP32 map over all 2^24 distinct values, the FP64 map on
+random words.
+"""
+import numpy as np
+import pytest
+
+from helpers import ordered_f32, to_numpy, ulp_distance_f32
+
+import paper_2310_19925_b300 as orand
+from paper_2310_19925_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def gpu_normals(torch, w0, w1):
+    words = np.empty(2 * len(w0), np.uint32)
+    words[0::2], words[1::2] = w0, w1
+    t = torch.from_numpy(words.view(np.int32)).cuda()
+    z = orand.map_words(W.F32_NORMAL, t)
+    torch.cuda.synchronize()
+    return to_numpy(z).reshape(-1, 2)
+
+
+def test_radius_all_u1(torch_cuda, orc):
+    rng = np.random.default_rng(1)
+    k = np.arange(1 << 24, dtype=np.uint32)
+    w0 = (k << 8) | rng.integers(0, 256, k.size, dtype=np.uint32)
+    w1 = rng.integers(0, 256, k.size, dtype=np.uint32)           # u2 = 0
+    z = gpu_normals(torch_cuda, w0, w1)
+    ref = orc.box_muller_array(w0, w1)
+    assert np.all(z[:, 1] == 0.0)
+    d = ulp_distance_f32(z[:, 0], ref[:, 0])
+    assert d.max() <= 2, "radius max ulp %d at k=%d" % (d.max(), int(k[d.argmax()]))
+    assert z[-1, 0] == 0.0 and not np.signbit(z[-1, 0])          # u1 = 1 gives +0
+
+
+def test_trig_all_u2(torch_cuda, orc):
+    m = np.arange(1 << 24, dtype=np.uint32)
+    w1 = m << 8
+    w0 = np.full(m.size, 0x7FFFFF00, np.uint32)                  # u1 = 1/2: r = sqrt(2 ln 2)
+    z = gpu_normals(torch_cuda, w0, w1)
+    ref = orc.box_muller_array(w0, w1)
+    for c in (0, 1):
+        d = ulp_distance_f32(z[:, c], ref[:, c])
+        assert d.max() <= 4, "component %d max ulp %d at m=%d" % (c, d.max(), int(m[d.argmax()]))
+    quarter = np.array([0, 1 << 22, 2 << 22, 3 << 22])
+    assert np.all(ordered_f32(z[quarter, 0][[1, 3]]) == 0) and np.all(ordered_f32(z[quarter, 1][[0, 2]]) == 0)
+
+
+def test_normals_random_pairs(torch_cuda, orc):
+    rng = np.random.default_rng(2)
+    w = rng.integers(0, 2**32, (1 << 24, 2), dtype=np.uint64).astype(np.uint32)
+    z = gpu_normals(torch_cuda, w[:, 0], w[:, 1])
+    ref = orc.box_muller_array(w[:, 0], w[:, 1])
+    d = ulp_distance_f32(z.ravel(), ref.ravel())
+    assert d.max() <= 4
+    assert (d > 2).mean() < 1e-5
+
+
+def test_uniform_maps_exact(torch_cuda, orc):
+    torch = torch_cuda
+    rng = np.random.default_rng(3)
+    k = np.arange(1 << 24, dtype=np.uint32)
+    w = (k << 8) | rng.integers(0, 256, k.size, dtype=np.uint32)
+    got = to_numpy(orand.map_words(W.F32_UNIFORM, torch.from_numpy(w.view(np.int32)).cuda()))
+    assert np.array_equal(got.astype(np.float64), orc.map_words(W.F32_UNIFORM, w))
+    w2 = rng.integers(0, 2**32, 1 << 22, dtype=np.uint64).astype(np.uint32)
+    w2[:8] = [0, 0, 0, 0x800, 0xFFFFFFFF, 0xFFFFFFFF, 0x80000000, 0]
+    got = to_numpy(orand.map_words(W.F64_UNIFORM, torch.from_numpy(w2.view(np.int32)).cuda()))
+    assert np.array_equal(got, orc.map_words(W.F64_UNIFORM, w2))
+    got = to_numpy(orand.map_words(W.U32, torch.from_numpy(w2.view(np.int32)).cuda()))
+    assert np.array_equal(got, w2)
+
+
+def test_map_words_odd_counts_match_fill(torch_cuda, orc):
+    torch = torch_cuda
+    for dtype in range(4):
+        for n in (1, 3, 5, 18):
+            words = orc.stream_words(W.PHILOX, 9, 2, 0, orc.words_for(dtype, n))
+            got = to_numpy(orand.map_words(dtype, torch.from_numpy(words.view(np.int32)).cuda(), n_values=n))
+            ref = orc.fill(W.PHILOX, dtype, 9, 2, 1, n)
+            if dtype == W.F32_NORMAL:
+                assert ulp_distance_f32(got, ref).max() <= 4
+            else:
+                assert np.array_equal(got.astype(ref.dtype), ref)
