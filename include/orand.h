@@ -40,7 +40,8 @@ typedef enum orand_status_t {
     ORAND_ERR_ALLOC = -4,           /* a context-owned allocation failed */
     ORAND_ERR_CUDA = -5,            /* a CUDA runtime call or launch failed */
     ORAND_ERR_DEVICE_TIMEOUT = -6,  /* a device-side wait gave up and set its error word */
-    ORAND_ERR_UNSUPPORTED = -7      /* current device is not the compiled target */
+    ORAND_ERR_UNSUPPORTED = -7,     /* current device is not the compiled target */
+    ORAND_ERR_SCRATCH_LIMIT = -8    /* request larger than a fixed, preallocated scratch area allows */
 } orand_status_t;
 
 typedef enum orand_gen_t {
@@ -188,6 +189,31 @@ orand_status_t orand_walk3d_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
 orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
                                 const double *grad_loss, double *dmu, double *dsigma, float *dx0,
                                 cudaStream_t stream);
+
+/* The adjoint above without a context and without any memory allocation.
+ * There is no counterpart in the paper; this entry point exists for callers
+ * that must not allocate device memory: code running under a host
+ * framework that owns the whole device memory budget, code whose device
+ * memory is capped so a new allocation could fail mid-run, and
+ * latency-sensitive code that cannot take the device-wide synchronisation
+ * cudaMalloc/cudaFree imply.
+ * Inputs and outputs are exactly those of orand_walk3d_bwd, with the same
+ * bits.  The per-block reduction partials live in a fixed 512 KiB array in
+ * the library's device memory, reserved when the library is loaded and held
+ * by every device that loads it until the process exits.  That bounds
+ * n_particles to at most 4,194,304 (2^22, one 256-thread block per 256
+ * particles).  Larger requests return ORAND_ERR_SCRATCH_LIMIT before
+ * anything is launched.
+ * The first call on a device looks up that array's device address (once
+ * per device, with that device current).  Make that first call before any
+ * stream capture on the device.
+ * All calls share the one array.  Every slot a call reads is written
+ * earlier in the same call, so nothing needs clearing between calls.  But
+ * calls that run at the same time on the GPU (other streams or threads)
+ * race on it: order them, for example on one stream.
+ * Errors: as orand_walk3d_bwd, plus ORAND_ERR_SCRATCH_LIMIT. */
+orand_status_t orand_walk3d_bwd_noalloc(const orand_walk3d_t *p, const float *xT, const double *grad_loss,
+                                        double *dmu, double *dsigma, float *dx0, cudaStream_t stream);
 
 /* Plain baseline of the same walk, in the paper's one-launch-per-step
  * pattern (Fig. 1 host loop).  It stores every noise draw: z_store is

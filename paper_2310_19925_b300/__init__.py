@@ -26,6 +26,7 @@ ORAND_OK = 0
 STATUS_NAMES = {
     0: "ORAND_OK", -1: "ORAND_ERR_INVALID_ARG", -2: "ORAND_ERR_OVERFLOW", -3: "ORAND_ERR_ALIGNMENT",
     -4: "ORAND_ERR_ALLOC", -5: "ORAND_ERR_CUDA", -6: "ORAND_ERR_DEVICE_TIMEOUT", -7: "ORAND_ERR_UNSUPPORTED",
+    -8: "ORAND_ERR_SCRATCH_LIMIT",
 }
 
 
@@ -60,6 +61,7 @@ _SIGS = {
     "orand_walk3d_init": (_i32, [_vp, _vp, _vp]),
     "orand_walk3d_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_walk3d_bwd_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_fill_ragged": (_i32, [_vp, _vp, _sz, _vp, _u64, _vp]),
@@ -267,6 +269,12 @@ def orand_walk3d_fwd(ctx, params, x0_ptr, xT_ptr, ckpt_ptr, loss_ptr, stream_han
 def orand_walk3d_bwd(ctx, params, xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dx0_ptr, stream_handle):
     _check(_lib().orand_walk3d_bwd(ctx, ctypes.byref(params), xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr,
                                    dx0_ptr, stream_handle), "orand_walk3d_bwd")
+
+
+def orand_walk3d_bwd_noalloc(params, xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dx0_ptr, stream_handle):
+    """The adjoint without a context or any allocation (fixed 2^22-particle scratch)."""
+    _check(_lib().orand_walk3d_bwd_noalloc(ctypes.byref(params), xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr,
+                                           dx0_ptr, stream_handle), "orand_walk3d_bwd_noalloc")
 
 
 def orand_walk3d_plain_fwd(ctx, params, x0_ptr, x_ptr, z_ptr, loss_ptr, stream_handle):

@@ -150,6 +150,8 @@ const char *orand_status_string(orand_status_t status)
     case ORAND_ERR_CUDA: return "ORAND_ERR_CUDA: CUDA runtime call or launch failed";
     case ORAND_ERR_DEVICE_TIMEOUT: return "ORAND_ERR_DEVICE_TIMEOUT: a device-side wait gave up";
     case ORAND_ERR_UNSUPPORTED: return "ORAND_ERR_UNSUPPORTED: device is not compute capability 10.3 (sm_103a)";
+    case ORAND_ERR_SCRATCH_LIMIT:
+        return "ORAND_ERR_SCRATCH_LIMIT: request exceeds the fixed scratch of the allocation-free entry point";
     }
     return "ORAND: unknown status";
 }

@@ -10,6 +10,8 @@
 // integer- and FP-pipe work per step, not bytes.
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "ctx.cuh"
 #include "orand_device.cuh"
@@ -476,3 +478,75 @@ orand_status_t orand_walk3d_plain_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ allocation-free adjoint
+//
+// orand_walk3d_bwd_noalloc: the adjoint with its reduction partials in a
+// fixed device array instead of context scratch, so no call ever allocates.
+
+namespace orand_impl {
+
+constexpr uint64_t kNoAllocMaxParticles = 1ull << 22;
+constexpr unsigned kNoAllocMaxBlocks = (unsigned)(kNoAllocMaxParticles / kWalkBlock);  // 16384
+
+// 16384 blocks x 4 FP64 partials = 512 KiB, resident on every device that
+// loads the library.
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * kRedWidth];
+
+constexpr int kNoAllocDevices = 64;
+static std::once_flag g_noalloc_once[kNoAllocDevices];
+static double *g_noalloc_ptr[kNoAllocDevices];
+static cudaError_t g_noalloc_err[kNoAllocDevices];
+
+// Device address of g_noalloc_partials on the current device, looked up once
+// per device (the host-side name is only a stand-in for that address).
+static orand_status_t noalloc_partials(double **out)
+{
+    int dev = -1;
+    ORAND_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocDevices) return ORAND_ERR_UNSUPPORTED;
+    std::call_once(g_noalloc_once[dev], [dev] {
+        void *p = nullptr;
+        g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        g_noalloc_ptr[dev] = (double *)p;
+    });
+    if (g_noalloc_err[dev] != cudaSuccess) {
+        log_cuda_failure("cudaGetSymbolAddress(g_noalloc_partials)", __FILE__, __LINE__, g_noalloc_err[dev]);
+        return cuda_status(g_noalloc_err[dev]);
+    }
+    *out = g_noalloc_ptr[dev];
+    return ORAND_OK;
+}
+
+}  // namespace orand_impl
+
+extern "C" orand_status_t orand_walk3d_bwd_noalloc(const orand_walk3d_t *p, const float *xT,
+                                                   const double *grad_loss, double *dmu, double *dsigma,
+                                                   float *dx0, cudaStream_t stream)
+{
+    Walk3dArgs a;
+    orand_status_t st = walk3d_args(p, &a);
+    if (st != ORAND_OK) return st;
+    if (a.n > kNoAllocMaxParticles) return ORAND_ERR_SCRATCH_LIMIT;
+    if ((st = check_ptr(dmu, 8)) != ORAND_OK || (st = check_ptr(dsigma, 8)) != ORAND_OK) return st;
+    if (a.n == 0) {
+        cudaError_t e = cudaMemsetAsync(dmu, 0, 3 * sizeof(double), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dsigma, 0, sizeof(double), stream);
+        return cuda_status(e);
+    }
+    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
+    if (dx0 && ((uintptr_t)dx0 % 4)) return ORAND_ERR_ALIGNMENT;
+    if (grad_loss && ((uintptr_t)grad_loss % 8)) return ORAND_ERR_ALIGNMENT;
+    DeviceInfo info;
+    if ((st = current_device(&info)) != ORAND_OK) return st;
+    double *partials = nullptr;
+    if ((st = noalloc_partials(&partials)) != ORAND_OK) return st;
+    // Every partial the reduction reads (blocks 0 .. grid-1) is written by
+    // this call's adjoint kernel first: no clearing needed.
+    const unsigned grid = walk_grid(a.n);
+    walk3d_bwd_kernel<<<grid, kWalkBlock, 0, stream>>>(a, xT, grad_loss, dx0, partials);
+    if ((st = launch_status()) != ORAND_OK) return st;
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
+    return launch_status();
+}
