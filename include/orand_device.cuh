@@ -238,17 +238,54 @@ __device__ __forceinline__ float u01_f32(uint32_t w)
     return __uint2float_rn(w >> 8) * 0x1p-24f;
 }
 
-/* ((hi:lo) >> 11) * 2^-53, exact, in [0, 1).  Built from integer ops
- * (leading-zero count, shift, exponent insert) rather than an integer to
- * FP64 conversion. */
+/* ((hi:lo) >> 11) * 2^-53, exact, in [0, 1).  Built from 32-bit integer ops
+ * (leading-zero count, funnel shifts, exponent insert) rather than an
+ * integer-to-FP64 conversion, which would run on the narrow FP64 pipe.
+ * The branch on mh == 0 (probability 2^-21) is almost never taken, which is
+ * cheapest for throughput-bound kernels. */
 __device__ __forceinline__ double u01_f64(uint32_t hi, uint32_t lo)
 {
-    const uint64_t m = ((((uint64_t)hi) << 32) | lo) >> 11;    /* < 2^53 */
-    if (m == 0) return 0.0;
-    const int top = 63 - __clzll((long long)m);                /* 0..52 */
-    const uint64_t mant = (m << (52 - top)) & 0x000FFFFFFFFFFFFFull;
-    const uint64_t expo = (uint64_t)(top - 53 + 1023);
-    return __longlong_as_double((long long)((expo << 52) | mant));
+    const uint32_t mh = hi >> 11;                        /* m = mh:ml, 53 bits */
+    const uint32_t ml = (hi << 21) | (lo >> 11);
+    uint32_t rh, rl;
+    if (mh != 0) {
+        /* top bit of m at 52 - lz: shift m left by lz so it lands on bit 52,
+         * drop it (mask), insert the biased exponent 1022 - lz. */
+        const uint32_t lz = (uint32_t)__clz((int)mh) - 11u;    /* 0..20 */
+        rh = (__funnelshift_l(ml, mh, lz) & 0x000FFFFFu) | ((1022u - lz) << 20);
+        rl = ml << lz;
+    } else if (ml != 0) {
+        const uint32_t lz = (uint32_t)__clz((int)ml);           /* top bit at 31 - lz */
+        const uint32_t sh = lz + 21u;                           /* 21..52: to bit 52 */
+        const uint64_t v = ((uint64_t)ml << sh) & 0x000FFFFFFFFFFFFFull;
+        rh = (uint32_t)(v >> 32) | ((1001u - lz) << 20);
+        rl = (uint32_t)v;
+    } else {
+        rh = 0u;
+        rl = 0u;
+    }
+    return __hiloint2double((int)rh, (int)rl);
+}
+
+/* The same map without branches (selects only), for latency-bound code
+ * where a branch would stop the scheduler from overlapping it with an
+ * independent dependency chain.  Identical results. */
+__device__ __forceinline__ double u01_f64_nb(uint32_t hi, uint32_t lo)
+{
+    const uint32_t mh = hi >> 11;
+    const uint32_t ml = (hi << 21) | (lo >> 11);
+    /* leading zeros of m as a 64-bit value (64 when m = 0) */
+    const uint32_t lz64 = mh ? (uint32_t)__clz((int)mh) : 32u + (uint32_t)__clz((int)ml);
+    /* shift m left so its top bit lands on bit 52: sh = lz64 - 11 in 0..52 */
+    const uint32_t sh = lz64 - 11u;
+    const bool big = sh >= 32u;
+    const uint32_t s1 = sh & 31u;
+    const uint32_t th = big ? (ml << s1) : __funnelshift_l(ml, mh, s1);
+    const uint32_t tl = big ? 0u : (ml << s1);
+    /* drop the leading bit, insert the biased exponent 1022 - sh */
+    const uint32_t rh = (th & 0x000FFFFFu) | ((1022u - sh) << 20);
+    const bool zero = (mh | ml) == 0u;
+    return __hiloint2double(zero ? 0 : (int)rh, zero ? 0 : (int)tl);
 }
 
 /* ---------------------------------------------------------- Box-Muller */
@@ -284,10 +321,9 @@ __device__ __forceinline__ float bm_radius(uint32_t w0)
     const uint32_t bits = __float_as_uint(__uint2float_rn(k)); /* exact */
     int e = (int)(bits >> 23) - 127;
     uint32_t mb = (bits & 0x007FFFFFu) | 0x3F800000u;          /* f in [1, 2) */
-    if (mb >= 0x3FB504F3u) {                                   /* f >= sqrt(2): halve f */
-        mb -= 0x00800000u;
-        e += 1;
-    }
+    const uint32_t halve = mb >= 0x3FB504F3u ? 1u : 0u;       /* f >= sqrt(2): halve f */
+    mb -= halve << 23;
+    e += (int)halve;
     const float g = __uint_as_float(mb) - 1.0f;                /* exact */
     float p = fmaf(bm::PL8, g, bm::PL7);
     p = fmaf(p, g, bm::PL6);
@@ -300,7 +336,16 @@ __device__ __forceinline__ float bm_radius(uint32_t w0)
     const float lnf = fmaf(g * g, p, g);
     const float E = (float)(e - 24);                           /* ln u1 = E ln 2 + ln f */
     const float lnu = fmaf(E, bm::LN2_HI, fmaf(E, bm::LN2_LO, lnf));
-    return sqrtf(fmaf(-2.0f, lnu, 0.0f));                      /* +0 at u1 = 1 */
+    const float x = fmaf(-2.0f, lnu, 0.0f);                    /* -2 ln u1 >= +0 */
+    /* sqrt(x) without the special-case branch of the IEEE square root:
+     * y ~ 1/sqrt(x) from the hardware estimate, s = x y, then one Newton step
+     * on the exact residual x - s^2 (an FMA).  x is +0 or a normal number in
+     * [2^-23, 34], so no special case can occur; x = 0 gives 0 by the select. */
+    const float y = rsqrtf(x);
+    const float sx = x * y;
+    const float res = fmaf(-sx, sx, x);
+    const float r = fmaf(0.5f * y, res, sx);
+    return x > 0.0f ? r : 0.0f;
 }
 
 /* (cos, sin)(2 pi u2), u2 = (w1 >> 8) * 2^-24: quadrant q = round(4 u2),

@@ -39,7 +39,8 @@ struct RaggedReq {
     uint64_t out_off;     // bytes from out_base
     uint64_t first_item;  // first chunk item (random-access requests)
     uint32_t counter;
-    uint8_t gen, dtype, vec, pad;
+    uint8_t gen, dtype, vec;
+    uint8_t raw;          // Tyche lane stores raw words; the convert pass maps them in place
 };
 static_assert(sizeof(RaggedReq) == 40, "RaggedReq layout");
 
@@ -50,6 +51,9 @@ struct RaggedHeader {
     uint64_t n_items;
     uint64_t chunk_values;
     uint64_t off_reqs, off_items, off_tyche, off_cursors;  // bytes from the table start
+    uint64_t off_conv;                                     // convert items: request index each
+    uint64_t n_conv_items;
+    uint64_t conv_chunk_groups;                            // groups per convert item
     uint32_t n_ty_items;                                   // Tyche warp items (32 slots each)
     uint32_t pad;
 };
@@ -94,32 +98,48 @@ __device__ __forceinline__ uint4 tyche_next4(orand::TycheState &st)
 }
 
 // One lane serves one whole Tyche request.  The MIX chain is the critical
-// path, so the next group's words are generated before the current group is
-// converted and stored: the two are independent and the scheduler overlaps
-// them.
+// path (one dependent chain of ~12 integer ops per word), so the lane is
+// software-pipelined in batches of kTycheBatch groups: while the chain
+// produces the words of batch k+1, the independent conversion and stores of
+// batch k fill the issue slots the chain leaves idle.
+constexpr int kTycheBatch = 4;
+
 template <int DT, int SW>
 __device__ __forceinline__ void tyche_request(const RaggedReq &q, char *out)
 {
     constexpr uint64_t V = Vals<DT>::V;
     constexpr uint64_t E = DT == ORAND_F64_UNIFORM ? 8u : 4u;
     char *base = out + q.out_off;
-    const uint64_t L = q.length, full = L / V;
+    const uint64_t L = q.length, G = (L + V - 1) / V;
     orand::TycheState st = orand::tyche_init(q.seed, q.counter);
-    uint4 w = tyche_next4(st);
-    if (q.vec) {
-        for (uint64_t g = 0; g < full; ++g) {
-            const uint4 cur = w;
-            w = tyche_next4(st);
-            store16<SW>(base + g * V * E, group_bits<DT>(cur));
+    uint64_t g = 0;
+    if (q.raw) {
+        // Raw words for every complete group: each value of this dtype takes
+        // exactly the bytes of the words it is made from, so the convert pass
+        // maps them in place.  The lane runs the bare MIX chain.
+        const uint64_t full = L / V;
+        for (; g < full; ++g) store16<SW>(base + g * V * E, tyche_next4(st));
+    } else if (q.vec && G >= 2 * kTycheBatch) {
+        // Full batches [g, g + kTycheBatch) whose groups are all complete.
+        const uint64_t full = (L / V) / kTycheBatch * kTycheBatch;
+        uint4 cur[kTycheBatch];
+#pragma unroll
+        for (int i = 0; i < kTycheBatch; ++i) cur[i] = tyche_next4(st);
+        for (; g + 2 * kTycheBatch <= full; g += kTycheBatch) {
+            uint4 nxt[kTycheBatch];
+#pragma unroll
+            for (int i = 0; i < kTycheBatch; ++i) nxt[i] = tyche_next4(st);
+#pragma unroll
+            for (int i = 0; i < kTycheBatch; ++i) store16<SW>(base + (g + i) * V * E, group_bits<DT, true>(cur[i]));
+#pragma unroll
+            for (int i = 0; i < kTycheBatch; ++i) cur[i] = nxt[i];
         }
-    } else {
-        for (uint64_t g = 0; g < full; ++g) {
-            const uint4 cur = w;
-            w = tyche_next4(st);
-            store_bits_masked<DT>(base + g * V * E, g * V, L, group_bits<DT>(cur));
-        }
+        // The last full batch is already generated.
+#pragma unroll
+        for (int i = 0; i < kTycheBatch; ++i) store16<SW>(base + (g + i) * V * E, group_bits<DT, true>(cur[i]));
+        g += kTycheBatch;
     }
-    if (full * V < L) store_bits_masked<DT>(base + full * V * E, full * V, L, group_bits<DT>(w));
+    for (; g < G; ++g) store_bits_masked<DT>(base + g * V * E, g * V, L, group_bits<DT>(tyche_next4(st)));
 }
 
 template <int SW>
@@ -181,7 +201,13 @@ __global__ void ragged_kernel(char *table)
         wi = __shfl_sync(0xFFFFFFFFu, wi, 0);
         if (wi >= h.n_ty_items) break;
         const uint32_t r = tyche[wi * 32 + lane];
-        if (r != kNoRequest) tyche_request_rt<SW>(reqs[r], h.out);
+        if (r != kNoRequest) {
+            // A register copy: the output stores could alias the table as far
+            // as the compiler knows, so a reference would be re-read from
+            // global memory inside the chain loop.
+            const RaggedReq q = reqs[r];
+            tyche_request_rt<SW>(q, h.out);
+        }
     }
     // Phase 2: chunks of the random-access requests.
     for (;;) {
@@ -198,6 +224,45 @@ __global__ void ragged_kernel(char *table)
         case ORAND_PHILOX4x32_10: chunk_dt<ORAND_PHILOX4x32_10, SW>(q, h.out, g0, g1, lane); break;
         case ORAND_THREEFRY4x32_20: chunk_dt<ORAND_THREEFRY4x32_20, SW>(q, h.out, g0, g1, lane); break;
         default: chunk_dt<ORAND_SQUARES32, SW>(q, h.out, g0, g1, lane); break;
+        }
+    }
+}
+
+// In-place conversion of the raw words Tyche lanes stored: each warp takes
+// one item (conv_chunk_groups complete groups of one request), loads each
+// group's four words and stores its values over them.
+template <int DT>
+__device__ __forceinline__ void convert_groups(char *base, uint64_t g0, uint64_t g1, int lane)
+{
+    constexpr uint64_t V = Vals<DT>::V;
+    constexpr uint64_t E = DT == ORAND_F64_UNIFORM ? 8u : 4u;
+    for (uint64_t g = g0 + lane; g < g1; g += 32) {
+        uint4 *p = reinterpret_cast<uint4 *>(base + g * V * E);
+        *p = group_bits<DT>(*p);
+    }
+}
+
+__global__ void ragged_convert_kernel(char *table)
+{
+    const RaggedHeader h = *reinterpret_cast<const RaggedHeader *>(table);
+    const RaggedReq *reqs = reinterpret_cast<const RaggedReq *>(table + h.off_reqs);
+    const uint32_t *conv = reinterpret_cast<const uint32_t *>(table + h.off_conv);
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t it = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); it < h.n_conv_items;
+         it += warps) {
+        const uint32_t r = conv[it];
+        const RaggedReq q = reqs[r];
+        const uint64_t V = q.dtype == ORAND_F64_UNIFORM ? 2u : 4u;
+        // items of one request are consecutive; its first item index is
+        // first_item (set on the host for raw Tyche requests)
+        const uint64_t g0 = (it - q.first_item) * h.conv_chunk_groups;
+        const uint64_t g1 = min(q.length / V, g0 + h.conv_chunk_groups);
+        char *base = h.out + q.out_off;
+        switch (q.dtype) {
+        case ORAND_F32_UNIFORM: convert_groups<ORAND_F32_UNIFORM>(base, g0, g1, lane); break;
+        case ORAND_F64_UNIFORM: convert_groups<ORAND_F64_UNIFORM>(base, g0, g1, lane); break;
+        default: convert_groups<ORAND_F32_NORMAL>(base, g0, g1, lane); break;
         }
     }
 }
@@ -263,14 +328,17 @@ void ragged_state_free(orand_ctx_t ctx)
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+constexpr uint64_t kConvChunkGroups = 2048;  // 32 KiB of output per convert item
+
 struct Plan {
     uint64_t chunk_values = 0;
+    std::vector<uint32_t> conv;   // convert items: request index each
     std::vector<RaggedReq> reqs;
     std::vector<uint32_t> tyche;  // warp items of 32 slots, kNoRequest-padded
     uint64_t n_tyche = 0;
     uint64_t n_items = 0;
     uint64_t total_values = 0;
-    size_t off_reqs = 256, off_items = 0, off_tyche = 0, off_cursors = 0, table_bytes = 0;
+    size_t off_reqs = 256, off_items = 0, off_tyche = 0, off_conv = 0, off_cursors = 0, table_bytes = 0;
 };
 
 static uint64_t words_for(uint32_t dt, uint64_t len)
@@ -287,6 +355,7 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
     p->chunk_values = chunk_values;
     p->reqs.resize(n);
     p->tyche.clear();
+    p->conv.clear();
     p->n_tyche = 0;
     std::vector<uint32_t> ty[4];
     p->n_items = 0;
@@ -309,7 +378,7 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
         d.gen = (uint8_t)q.gen;
         d.dtype = (uint8_t)q.dtype;
         d.vec = (((uintptr_t)out_base + q.out_offset_bytes) % 16 == 0) ? 1 : 0;
-        d.pad = 0;
+        d.raw = 0;
         d.first_item = p->n_items;
         if (q.length && check_overlap) ranges.emplace_back(q.out_offset_bytes, q.out_offset_bytes + bytes);
         p->total_values += q.length;
@@ -317,6 +386,14 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
         if (q.gen == ORAND_TYCHE) {
             ty[q.dtype].push_back((uint32_t)i);
             ++p->n_tyche;
+            const uint64_t V = q.dtype == ORAND_F64_UNIFORM ? 2 : 4;
+            const uint64_t full = q.length / V;
+            if (q.dtype != ORAND_U32 && d.vec && full > 0) {
+                // raw words now, converted in place by the convert pass
+                d.raw = 1;
+                d.first_item = p->conv.size();
+                for (uint64_t c = 0; c < full; c += kConvChunkGroups) p->conv.push_back((uint32_t)i);
+            }
         } else {
             p->n_items += (q.length + chunk_values - 1) / chunk_values;
         }
@@ -352,7 +429,8 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
     p->off_reqs = 256;
     p->off_items = align_up(p->off_reqs + n * sizeof(RaggedReq), 256);
     p->off_tyche = align_up(p->off_items + p->n_items * sizeof(uint32_t), 256);
-    p->off_cursors = align_up(p->off_tyche + p->tyche.size() * sizeof(uint32_t), 256);
+    p->off_conv = align_up(p->off_tyche + p->tyche.size() * sizeof(uint32_t), 256);
+    p->off_cursors = align_up(p->off_conv + p->conv.size() * sizeof(uint32_t), 256);
     p->table_bytes = p->off_cursors + 256;
     return ORAND_OK;
 }
@@ -368,6 +446,9 @@ static void write_staging(const Plan &p, char *out, char *h)
     hd.off_tyche = p.off_tyche;
     hd.off_cursors = p.off_cursors;
     hd.n_ty_items = (uint32_t)(p.tyche.size() / 32);
+    hd.off_conv = p.off_conv;
+    hd.n_conv_items = p.conv.size();
+    hd.conv_chunk_groups = kConvChunkGroups;
     std::memset(h, 0, 256);
     std::memcpy(h, &hd, sizeof(hd));
     std::memcpy(h + p.off_reqs, p.reqs.data(), p.reqs.size() * sizeof(RaggedReq));
@@ -380,6 +461,7 @@ static void write_staging(const Plan &p, char *out, char *h)
         for (uint64_t c = 0; c < n_chunks; ++c) items[k++] = (uint32_t)i;
     }
     std::memcpy(h + p.off_tyche, p.tyche.data(), p.tyche.size() * sizeof(uint32_t));
+    std::memcpy(h + p.off_conv, p.conv.data(), p.conv.size() * sizeof(uint32_t));
     std::memset(h + p.off_cursors, 0, 256);
 }
 
@@ -451,11 +533,14 @@ static orand_status_t ragged_grid(const RaggedConfig &c, unsigned *grid)
     return ORAND_OK;
 }
 
+// The batch: the persistent kernel, then the in-place conversion of the raw
+// Tyche words (a no-op grid when there are none).
 static void launch_kernel(char *table, const RaggedConfig &c, unsigned grid, cudaStream_t stream)
 {
     if (c.store_bytes == 16) ragged_kernel<16><<<grid, c.block, 0, stream>>>(table);
     else if (c.store_bytes == 8) ragged_kernel<8><<<grid, c.block, 0, stream>>>(table);
     else ragged_kernel<4><<<grid, c.block, 0, stream>>>(table);
+    ragged_convert_kernel<<<grid, 256, 0, stream>>>(table);
 }
 
 static bool valid_config(const RaggedConfig &c)

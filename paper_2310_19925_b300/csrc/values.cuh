@@ -28,8 +28,9 @@ struct Vals {
 
 // The group's values as a 16-byte bit pattern, in memory order: 4 x u32,
 // 4 x f32 (uniform, or normals z0 z1 of pair (w.x, w.y) then of (w.z, w.w)),
-// or 2 x f64 (from (w.x, w.y) and (w.z, w.w)).
-template <int DT>
+// or 2 x f64 (from (w.x, w.y) and (w.z, w.w)).  BRANCH_FREE selects the
+// branch-free FP64 map (same bits) for latency-bound callers.
+template <int DT, bool BRANCH_FREE = false>
 __device__ __forceinline__ uint4 group_bits(uint4 w)
 {
     if (DT == ORAND_U32) return w;
@@ -37,8 +38,10 @@ __device__ __forceinline__ uint4 group_bits(uint4 w)
         return make_uint4(__float_as_uint(orand::u01_f32(w.x)), __float_as_uint(orand::u01_f32(w.y)),
                           __float_as_uint(orand::u01_f32(w.z)), __float_as_uint(orand::u01_f32(w.w)));
     if (DT == ORAND_F64_UNIFORM) {
-        const unsigned long long a = __double_as_longlong(orand::u01_f64(w.x, w.y));
-        const unsigned long long b = __double_as_longlong(orand::u01_f64(w.z, w.w));
+        const double da = BRANCH_FREE ? orand::u01_f64_nb(w.x, w.y) : orand::u01_f64(w.x, w.y);
+        const double db = BRANCH_FREE ? orand::u01_f64_nb(w.z, w.w) : orand::u01_f64(w.z, w.w);
+        const unsigned long long a = __double_as_longlong(da);
+        const unsigned long long b = __double_as_longlong(db);
         return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
     }
     const float2 p = orand::box_muller_f32(w.x, w.y);

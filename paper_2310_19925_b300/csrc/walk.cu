@@ -87,9 +87,12 @@ __global__ void __launch_bounds__(kWalkBlock) walk2d_kernel(uint64_t n, uint64_t
     float cx = 0.f, cy = 0.f;
     for (uint32_t t = 1; t <= steps; ++t) {
         w = keys.block(0u, t);
-        const float2 z = orand::box_muller_f32(w.x, w.y);
-        kahan_add(x, cx, s * z.x);
-        kahan_add(y, cy, s * z.y);
+        // s * (r cos, r sin) with the step scale folded into the radius.
+        const float rs = s * orand::bm_radius(w.x);
+        float c, sn;
+        orand::bm_cos_sin(w.y, &c, &sn);
+        kahan_add(x, cx, rs * c);
+        kahan_add(y, cy, rs * sn);
     }
     out[i] = make_float2(x, y);
 }
@@ -113,6 +116,21 @@ __device__ __forceinline__ void walk3d_normals(const orand::PhiloxKeys &keys, ui
     z[0] = a.x;
     z[1] = a.y;
     z[2] = orand::box_muller_cos_f32(w.z, w.w);
+}
+
+// sigma sqrt(dt) * (z0, z1, z2) with the scale folded into the two radii.
+__device__ __forceinline__ void walk3d_scaled_normals(const orand::PhiloxKeys &keys, uint32_t t_counter,
+                                                      float scale, float z[3])
+{
+    const uint4 w = keys.block(0u, t_counter);
+    const float ra = scale * orand::bm_radius(w.x);
+    const float rb = scale * orand::bm_radius(w.z);
+    float ca, sa, cb, sb;
+    orand::bm_cos_sin(w.y, &ca, &sa);
+    orand::bm_cos_sin(w.w, &cb, &sb);
+    z[0] = ra * ca;
+    z[1] = ra * sa;
+    z[2] = rb * cb;
 }
 
 __device__ __forceinline__ void walk3d_x0(const orand::PhiloxKeys &keys, float x[3])
@@ -162,9 +180,9 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_fwd_kernel(Walk3dArgs a, co
                 next_ck += a.K;
             }
             float z[3];
-            walk3d_normals(keys, t + 1u, z);
+            walk3d_scaled_normals(keys, t + 1u, a.sig_sqdt, z);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], fmaf(a.sig_sqdt, z[q], a.mu_dt[q]));
+            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], z[q] + a.mu_dt[q]);
         }
         xT[3 * i] = x[0];
         xT[3 * i + 1] = x[1];
