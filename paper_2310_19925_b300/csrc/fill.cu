@@ -52,20 +52,24 @@ __global__ void __launch_bounds__(256) fill_random_access_kernel(FillArgs a)
 
 // ------------------------------------------------ tiled TMA-store variant
 //
-// Each thread owns a "run" of R consecutive groups of one stream (R a power
-// of two <= 8 dividing the groups per stream G), so per-stream setup (the
-// ten Philox round keys, the Threefry key schedule, the Squares key hash) is
-// paid once per R groups.  Runs are consecutive in memory, so the 256 runs
-// of a CTA form one contiguous tile of 256 * R * 16 bytes: the threads write
-// their groups into a shared-memory tile and one thread streams it to HBM
-// with a bulk asynchronous copy (cp.async.bulk, TMA engine), double-buffered
-// so the next tile is generated while the previous one drains.
+// Each thread owns "runs" of R consecutive groups of one stream (R a power of
+// two <= 8 dividing the groups per stream G), so per-stream setup (the ten
+// Philox round keys, the Threefry key schedule, the Squares key hash) is paid
+// once per R groups.  Runs are consecutive in memory.  A CTA of T threads
+// fills one contiguous tile of T * TR runs (TR runs per thread) in shared
+// memory, and one thread streams it to HBM with a bulk asynchronous copy
+// (cp.async.bulk, the TMA engine).  The copy is double-buffered, so the next
+// tile is generated while the previous one drains.
 //
-// Shared-memory bank conflicts: thread x writes 16-byte slot x*R + j.  At
-// step i it handles j = (i + (x >> log2(8/R))) mod R, which puts the eight
-// threads of each 128-byte store phase on eight distinct bank groups.
-
-constexpr int kTileThreads = 256;
+// Launch shape per row (measured on B300): the light, HBM-bound Philox u32 and
+// FP32-uniform fills use T = 128 and TR = 8 / R, which halves the per-tile
+// barrier and bookkeeping cost per group.  Every other fill is bound by the
+// integer or FMA pipes and keeps T = 256, TR = 1, for more warps per SM.
+//
+// Shared-memory bank conflicts: thread x writes 16-byte slots (k*T + x)*R + j.
+// At step i it handles j = (i + (x >> log2(8/R))) mod R, which puts the eight
+// threads of each 128-byte store phase on eight distinct bank groups.  k*T*R
+// slots is a multiple of 128 bytes, so each extra run keeps the pattern.
 
 __device__ __forceinline__ void bulk_store_s2g(void *gdst, const void *ssrc, uint32_t bytes)
 {
@@ -81,7 +85,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 struct TileArgs {
     uint64_t seed;
     uint64_t n_runs;      // n_streams * G / R
-    uint64_t n_tiles;     // ceil(n_runs / 256)
+    uint64_t n_tiles;     // ceil(n_runs / (T * TR))
     uint64_t rps;         // runs per stream = G / R
     int rps_shift;        // log2(rps) when rps is a power of two, else -1
     uint32_t counter;
@@ -120,55 +124,65 @@ struct StreamGen<ORAND_SQUARES32> {
     __device__ __forceinline__ uint4 group(uint32_t b) const { return orand::squares_block(key, counter, b); }
 };
 
+// Run r: groups [q*R, q*R + R) of stream s, written to slots [slot*R, slot*R + R).
 template <int GEN, int DT, int R>
-__global__ void __launch_bounds__(kTileThreads) fill_tile_kernel(TileArgs a)
+__device__ __forceinline__ void fill_run(const TileArgs &a, uint64_t r, int x, uint4 *sm, uint64_t slot)
 {
-    extern __shared__ __align__(128) uint4 tile[];  // 2 buffers of kTileThreads * R groups
     constexpr int ROT_SHIFT = R == 8 ? 0 : R == 4 ? 1 : R == 2 ? 2 : 3;
+    uint64_t s, q;
+    if (a.rps_shift >= 0) {
+        s = r >> a.rps_shift;
+        q = r & (a.rps - 1);
+    } else {
+        s = r / a.rps;
+        q = r - s * a.rps;
+    }
+    if constexpr (GEN == ORAND_TYCHE) {
+        // Whole stream in one run (R == G): sequential words, slot order.
+        orand::TycheState st = orand::tyche_init(a.seed ^ s, a.counter);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            uint4 w;
+            w.x = orand::tyche_next(st);
+            w.y = orand::tyche_next(st);
+            w.z = orand::tyche_next(st);
+            w.w = orand::tyche_next(st);
+            sm[slot * R + j] = group_bits<DT>(w);
+        }
+    } else {
+        const StreamGen<GEN> sg(a.seed ^ s, a.counter);
+        const uint32_t b0 = (uint32_t)(q * R);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int j = (i + (x >> ROT_SHIFT)) & (R - 1);
+            sm[slot * R + j] = group_bits<DT>(sg.group(b0 + (uint32_t)j));
+        }
+    }
+}
+
+template <int GEN, int DT, int R, int T, int TR>
+__global__ void __launch_bounds__(T) fill_tile_kernel(TileArgs a)
+{
+    constexpr uint64_t kRunsPerTile = (uint64_t)T * TR;
+    extern __shared__ __align__(128) uint4 tile[];          // 2 buffers of kRunsPerTile * R groups
     const int x = threadIdx.x;
     int buf = 0;
     for (uint64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        uint4 *sm = tile + buf * (kTileThreads * R);
+        uint4 *sm = tile + buf * (kRunsPerTile * R);
         // The bulk copy issued two tiles ago read this buffer; wait until it has.
         if (x == 0) bulk_wait_read_1();
         __syncthreads();
-        const uint64_t r = t * kTileThreads + x;
-        if (r < a.n_runs) {
-            uint64_t s, q;
-            if (a.rps_shift >= 0) {
-                s = r >> a.rps_shift;
-                q = r & (a.rps - 1);
-            } else {
-                s = r / a.rps;
-                q = r - s * a.rps;
-            }
-            if constexpr (GEN == ORAND_TYCHE) {
-                // Whole stream in one run (R == G): sequential words, slot order.
-                orand::TycheState st = orand::tyche_init(a.seed ^ s, a.counter);
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    uint4 w;
-                    w.x = orand::tyche_next(st);
-                    w.y = orand::tyche_next(st);
-                    w.z = orand::tyche_next(st);
-                    w.w = orand::tyche_next(st);
-                    sm[x * R + j] = group_bits<DT>(w);
-                }
-            } else {
-                const StreamGen<GEN> sg(a.seed ^ s, a.counter);
-                const uint32_t b0 = (uint32_t)(q * R);
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const int j = (i + (x >> ROT_SHIFT)) & (R - 1);
-                    sm[x * R + j] = group_bits<DT>(sg.group(b0 + (uint32_t)j));
-                }
-            }
+        for (int k = 0; k < TR; ++k) {
+            const uint64_t slot = (uint64_t)k * T + x;
+            const uint64_t r = t * kRunsPerTile + slot;
+            if (r < a.n_runs) fill_run<GEN, DT, R>(a, r, x, sm, slot);
         }
         fence_proxy_async_smem();
         __syncthreads();
         if (x == 0) {
-            const uint64_t r0 = t * kTileThreads;
-            const uint64_t runs = min((uint64_t)kTileThreads, a.n_runs - r0);
+            const uint64_t r0 = t * kRunsPerTile;
+            const uint64_t runs = min(kRunsPerTile, a.n_runs - r0);
             bulk_store_s2g(a.out + r0 * R, sm, (uint32_t)(runs * R * 16));
             bulk_commit();
         }
@@ -195,26 +209,35 @@ __global__ void __launch_bounds__(256) fill_tyche_kernel(FillArgs a)
     }
 }
 
-template <int GEN, int DT, int R>
-static orand_status_t launch_tile_r(const TileArgs &a, const DeviceInfo &info, cudaStream_t stream)
+template <int GEN, int DT, int R, int T, int TR>
+static orand_status_t launch_tile_shape(TileArgs a, const DeviceInfo &info, cudaStream_t stream)
 {
-    const size_t smem = 2u * kTileThreads * R * sizeof(uint4);
+    const size_t smem = 2u * (size_t)T * TR * R * sizeof(uint4);
     static bool configured = false;  // per instantiation; idempotent, so a race is harmless
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(fill_tile_kernel<GEN, DT, R>,
+        cudaError_t e = cudaFuncSetAttribute(fill_tile_kernel<GEN, DT, R, T, TR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
         configured = true;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_tile_kernel<GEN, DT, R>,
-                                                                  kTileThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_tile_kernel<GEN, DT, R, T, TR>, T,
+                                                                  smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) per_sm = 1;
+    a.n_tiles = ceil_div(a.n_runs, (uint64_t)T * TR);
     uint64_t grid = (uint64_t)per_sm * info.sm_count;
     if (grid > a.n_tiles) grid = a.n_tiles;
-    fill_tile_kernel<GEN, DT, R><<<(unsigned)grid, kTileThreads, smem, stream>>>(a);
+    fill_tile_kernel<GEN, DT, R, T, TR><<<(unsigned)grid, T, smem, stream>>>(a);
     return launch_status();
+}
+
+template <int GEN, int DT, int R>
+static orand_status_t launch_tile_r(const TileArgs &a, const DeviceInfo &info, cudaStream_t stream)
+{
+    constexpr bool light = GEN == ORAND_PHILOX4x32_10 && (DT == ORAND_U32 || DT == ORAND_F32_UNIFORM);
+    if constexpr (light) return launch_tile_shape<GEN, DT, R, 128, 8 / R>(a, info, stream);
+    else return launch_tile_shape<GEN, DT, R, 256, 1>(a, info, stream);
 }
 
 template <int GEN, int DT>
@@ -324,7 +347,7 @@ orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uin
             t.counter = counter;
             t.rps = G / R;
             t.n_runs = n_streams * t.rps;
-            t.n_tiles = ceil_div(t.n_runs, kTileThreads);
+            t.n_tiles = 0;  // set per launch shape
             t.rps_shift = (t.rps & (t.rps - 1)) == 0 ? __builtin_ctzll(t.rps) : -1;
             t.out = (uint4 *)out;
             switch (gen) {
