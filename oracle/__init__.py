@@ -81,6 +81,8 @@ def lib():
         L.orc_fill.restype = ctypes.c_int
         L.orc_walk2d.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                  ctypes.c_float, ctypes.c_float, dp, dp]
+        L.orc_langevin2d.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         L.orc_walk3d_init.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, dp]
         L.orc_walk3d_forward.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, fp,
@@ -263,6 +265,24 @@ def walk2d(seed: int, n: int, steps: int, dt: float, D: float, p_first: int = 0,
             for f in [ex.submit(run, a, b) for a, b in parts]:
                 f.result()
     return x0, xT
+
+
+def langevin2d(seed, n, steps, dt=1e-3, gamma=1.0, mass=1.0, p_first=0, threads=1):
+    """The paper's FP64 Brownian-dynamics benchmark (Fig. 1): returns (n, 4) = x, y, vx, vy."""
+    st = np.zeros((n, 4), np.float64)
+
+    def run(a, b):
+        lib().orc_langevin2d(seed, p_first + a, b - a, steps, dt, gamma, mass, _dp(st[a:b]))
+
+    parts = _split(n, threads)
+    if len(parts) <= 1:
+        for a, b in parts:
+            run(a, b)
+    else:
+        with ThreadPoolExecutor(len(parts)) as ex:
+            for f in [ex.submit(run, a, b) for a, b in parts]:
+                f.result()
+    return st
 
 
 def walk3d_init(seed: int, n: int, p_first: int = 0) -> np.ndarray:

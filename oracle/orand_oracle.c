@@ -502,3 +502,49 @@ void orc_walk3d_adjoint(uint64_t seed, uint64_t p_first, uint64_t n, uint32_t st
         *dsigma += gsig;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * The paper's Brownian-dynamics macro-benchmark (Fig. 1, §5): particles with
+ * velocity drag and a uniform random kick per step, FP64.  Particle p has
+ * key64 = seed ^ p.  Counter 0 initialises it: (x, y) = draw_double2, i.e.
+ * the two FP64 uniforms of the Philox block with counter (0, 0, 0, 0) (words
+ * 0-1 and 2-3, first word high, as in Fig. 3), and v = 0.  Step `iter`
+ * (1..steps) then does, in this order and in FP64:
+ *     vx -= gamma / mass * vx * dt        (and vy)
+ *     (rx, ry) = draw_double2 of block (0, iter, 0, 0)
+ *     vx += (rx * 2 - 1) * sqrt_dt        (and vy)
+ *     x  += vx * dt                       (and y)
+ * gamma / mass and sqrt(dt) are evaluated once.  The position update is this
+ * build's reading: Fig. 1 elides it ("...").  state: [n][4] = x, y, vx, vy.
+ * ---------------------------------------------------------------------- */
+void orc_langevin2d(uint64_t seed, uint64_t p_first, uint64_t n, uint32_t steps, double dt, double gamma,
+                    double mass, double *state)
+{
+    const double g_over_m = gamma / mass;
+    const double sqrt_dt = sqrt(dt);
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t key64 = seed ^ (p_first + i);
+        const uint32_t key[2] = {(uint32_t)(key64 & 0xFFFFFFFFull), (uint32_t)(key64 >> 32)};
+        uint32_t ctr0[4] = {0u, 0u, 0u, 0u}, blk[4];
+        orc_philox4x32_10(ctr0, key, blk);
+        double x = orc_f64_uniform(blk[0], blk[1]);
+        double y = orc_f64_uniform(blk[2], blk[3]);
+        double vx = 0.0, vy = 0.0;
+        for (uint32_t iter = 1; iter <= steps; ++iter) {
+            vx = vx - g_over_m * vx * dt;
+            vy = vy - g_over_m * vy * dt;
+            uint32_t ctr[4] = {0u, iter, 0u, 0u};
+            orc_philox4x32_10(ctr, key, blk);
+            const double rx = orc_f64_uniform(blk[0], blk[1]);
+            const double ry = orc_f64_uniform(blk[2], blk[3]);
+            vx = vx + (rx * 2.0 - 1.0) * sqrt_dt;
+            vy = vy + (ry * 2.0 - 1.0) * sqrt_dt;
+            x = x + vx * dt;
+            y = y + vy * dt;
+        }
+        state[4 * i] = x;
+        state[4 * i + 1] = y;
+        state[4 * i + 2] = vx;
+        state[4 * i + 3] = vy;
+    }
+}

@@ -466,3 +466,35 @@ def test_walk3d_adjoint_closed_form(orc):
     assert dsig == pytest.approx(k * math.sqrt(W3["dt"]) * float((xT * S).sum()) / n, rel=1e-12)
     assert np.allclose(dx0, k * xT / n, rtol=0, atol=1e-15)
     assert orc.walk3d_loss(xT, k, n) == pytest.approx(0.5 * k * float((xT ** 2).sum()) / n, rel=1e-14)
+
+
+# ------------------------------------------------- Langevin macro-benchmark --
+
+def test_langevin_without_drag_is_a_sum_of_kicks(orc):
+    # gamma = 0: v_T = sqrt(dt) * sum_t (2 r_t - 1), x_T = x_0 + dt * sum_t v_t.
+    n, steps, dt = 3, 40, 1e-3
+    st = orc.langevin2d(0, n, steps, dt=dt, gamma=0.0, p_first=50)
+    for i in range(n):
+        pid = 50 + i
+        b0 = orc.philox4x32_10((0, 0, 0, 0), (pid, 0))
+        x = orc.f64_uniform(b0[0], b0[1])
+        vx, xs = 0.0, []
+        kicks = []
+        for t in range(1, steps + 1):
+            b = orc.philox4x32_10((0, t, 0, 0), (pid, 0))
+            kicks.append(orc.f64_uniform(b[0], b[1]) * 2 - 1)
+            xs.append(math.fsum(kicks) * math.sqrt(dt))
+        assert st[i, 2] == pytest.approx(xs[-1], abs=1e-15)
+        assert st[i, 0] == pytest.approx(x + dt * math.fsum(xs), abs=1e-14)
+
+
+def test_langevin_stationary_velocity_variance(orc):
+    # v <- c v + xi with c = 1 - gamma dt / m and xi uniform on [-sqrt dt, sqrt dt]:
+    # stationary Var(v) = (dt / 3) / (1 - c^2).
+    n, steps, dt, gamma = 4096, 4000, 1e-3, 1.0
+    st = orc.langevin2d(0, n, steps, dt=dt, gamma=gamma, threads=8)
+    v = st[:, 2:].ravel()
+    c = 1 - gamma * dt
+    var = (dt / 3) / (1 - c * c)
+    assert abs(v.var() / var - 1) < 5 * math.sqrt(2 / v.size)
+    assert abs(v.mean()) < 5 * math.sqrt(var / v.size)
