@@ -291,6 +291,63 @@ typedef struct orand_ragged_stats_t {
 } orand_ragged_stats_t;
 orand_status_t orand_ragged_stats(orand_ctx_t ctx, orand_ragged_stats_t *stats);
 
+/* ------------------------------------------------------------------------
+ * The paper's Brownian-dynamics macro-benchmark (Fig. 1, §5): 2D particles
+ * with velocity drag and a uniform FP64 kick per step.  Particle i has
+ * pid = p_first + i and key seed ^ pid.  Counter 0 sets (x, y) =
+ * draw_double2 (the two FP64 uniforms of one Philox block, first word
+ * high) and v = 0.  Step `iter` does, in FP64 with round-to-nearest and no
+ * fused multiply-add:
+ *     v -= gamma / mass * v * dt;  r = draw_double2(pid, iter);
+ *     v += (r * 2 - 1) * sqrt(dt);  x += v * dt
+ * (the position update is this library's reading; Fig. 1 elides it).
+ * particles: n_particles orand_particle_t (array of structures, 8-byte
+ * aligned).
+ * ---------------------------------------------------------------------- */
+typedef struct orand_particle_t {
+    double x, y, vx, vy;
+    uint64_t pid;
+} orand_particle_t;
+
+typedef struct orand_langevin2d_t {
+    uint64_t n_particles;
+    uint64_t p_first;
+    uint64_t seed;
+    double dt;
+    double gamma;
+    double mass;
+} orand_langevin2d_t;
+
+/* Counter-0 initialisation (the paper's init_particles). */
+orand_status_t orand_langevin2d_init(const orand_langevin2d_t *p, orand_particle_t *particles, cudaStream_t stream);
+/* One step with counter `counter`, one launch: the paper's Fig. 1 host loop
+ * calls this for counter = 1..STEPS. */
+orand_status_t orand_langevin2d_step(const orand_langevin2d_t *p, orand_particle_t *particles, uint32_t counter,
+                                     cudaStream_t stream);
+/* The Fig. 1 host loop: orand_langevin2d_step for counters first_counter ..
+ * first_counter + steps - 1, one launch each. */
+orand_status_t orand_langevin2d_run_per_step(const orand_langevin2d_t *p, orand_particle_t *particles,
+                                             uint32_t first_counter, uint32_t steps, cudaStream_t stream);
+/* Steps with counters first_counter .. first_counter + steps - 1 in one
+ * launch, with the state in registers.  Same bits as the same sequence of
+ * orand_langevin2d_step calls.  ORAND_ERR_OVERFLOW if the counters pass
+ * 2^32. */
+orand_status_t orand_langevin2d_fused(const orand_langevin2d_t *p, orand_particle_t *particles,
+                                      uint32_t first_counter, uint32_t steps, cudaStream_t stream);
+/* The comparison system of §5, in the cuRAND pattern of Fig. 2: one
+ * curandStatePhilox4_32_10_t per particle, set up by
+ * curand_init(curand_seed, pid, 0), and initial positions drawn from it.
+ * Each step then loads and stores the state.  states: n_particles states of
+ * orand_langevin2d_curand_state_bytes() each, 16-byte aligned, caller-owned. */
+size_t orand_langevin2d_curand_state_bytes(void);
+orand_status_t orand_langevin2d_curand_setup(const orand_langevin2d_t *p, orand_particle_t *particles, void *states,
+                                             uint64_t curand_seed, cudaStream_t stream);
+orand_status_t orand_langevin2d_curand_step(const orand_langevin2d_t *p, orand_particle_t *particles, void *states,
+                                            cudaStream_t stream);
+/* The Fig. 2 host loop: `steps` calls of orand_langevin2d_curand_step. */
+orand_status_t orand_langevin2d_curand_run(const orand_langevin2d_t *p, orand_particle_t *particles, void *states,
+                                           uint32_t steps, cudaStream_t stream);
+
 #ifdef __cplusplus
 }  /* extern "C" */
 #endif

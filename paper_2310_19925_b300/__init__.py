@@ -64,6 +64,14 @@ _SIGS = {
     "orand_walk3d_bwd_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_langevin2d_init": (_i32, [_vp, _vp, _vp]),
+    "orand_langevin2d_step": (_i32, [_vp, _vp, _u32, _vp]),
+    "orand_langevin2d_fused": (_i32, [_vp, _vp, _u32, _u32, _vp]),
+    "orand_langevin2d_run_per_step": (_i32, [_vp, _vp, _u32, _u32, _vp]),
+    "orand_langevin2d_curand_run": (_i32, [_vp, _vp, _vp, _u32, _vp]),
+    "orand_langevin2d_curand_state_bytes": (_sz, []),
+    "orand_langevin2d_curand_setup": (_i32, [_vp, _vp, _vp, _u64, _vp]),
+    "orand_langevin2d_curand_step": (_i32, [_vp, _vp, _vp, _vp]),
     "orand_fill_ragged": (_i32, [_vp, _vp, _sz, _vp, _u64, _vp]),
     "orand_fill_ragged_serial": (_i32, [_vp, _sz, _vp, _u64, _vp]),
     "orand_ragged_set_config": (_i32, [_vp, _vp]),
@@ -94,6 +102,14 @@ class Walk3DParams(ctypes.Structure):
                 ("steps", _u32), ("ckpt_every", _u32), ("dt", _f32), ("mu", _f32 * 3), ("sigma", _f32),
                 ("k", _f32)]
 
+
+class Langevin2DParams(ctypes.Structure):
+    """orand_langevin2d_t."""
+    _fields_ = [("n_particles", _u64), ("p_first", _u64), ("seed", _u64), ("dt", _f64), ("gamma", _f64),
+                ("mass", _f64)]
+
+
+PARTICLE_BYTES = 40  # orand_particle_t: x, y, vx, vy (double), pid (uint64)
 
 assert ctypes.sizeof(Walk2DParams) == 40 and ctypes.sizeof(Walk3DParams) == 64
 
@@ -429,3 +445,59 @@ def fill_ragged(requests, out=None, out_bytes=None, serial=False, ctx=None, stre
         c = (ctx or default_context()).handle
         orand_fill_ragged(c, reqs.ctypes.data, len(reqs), _ptr(out), nbytes, sh)
     return out
+
+
+# -------------------------------------------- paper macro-benchmark (Fig. 1) --
+
+def langevin2d_params(n_particles, dt=1e-3, gamma=1.0, mass=1.0, seed=0, p_first=0) -> Langevin2DParams:
+    return Langevin2DParams(n_particles, p_first, seed & (2**64 - 1), dt, gamma, mass)
+
+
+def orand_langevin2d_init(params, particles_ptr, stream_handle):
+    _check(_lib().orand_langevin2d_init(ctypes.byref(params), particles_ptr, stream_handle), "orand_langevin2d_init")
+
+
+def orand_langevin2d_step(params, particles_ptr, counter, stream_handle):
+    _check(_lib().orand_langevin2d_step(ctypes.byref(params), particles_ptr, counter, stream_handle),
+           "orand_langevin2d_step")
+
+
+def orand_langevin2d_fused(params, particles_ptr, first_counter, steps, stream_handle):
+    _check(_lib().orand_langevin2d_fused(ctypes.byref(params), particles_ptr, first_counter, steps, stream_handle),
+           "orand_langevin2d_fused")
+
+
+def orand_langevin2d_run_per_step(params, particles_ptr, first_counter, steps, stream_handle):
+    _check(_lib().orand_langevin2d_run_per_step(ctypes.byref(params), particles_ptr, first_counter, steps,
+                                                stream_handle), "orand_langevin2d_run_per_step")
+
+
+def orand_langevin2d_curand_run(params, particles_ptr, states_ptr, steps, stream_handle):
+    _check(_lib().orand_langevin2d_curand_run(ctypes.byref(params), particles_ptr, states_ptr, steps, stream_handle),
+           "orand_langevin2d_curand_run")
+
+
+def orand_langevin2d_curand_state_bytes() -> int:
+    return int(_lib().orand_langevin2d_curand_state_bytes())
+
+
+def orand_langevin2d_curand_setup(params, particles_ptr, states_ptr, curand_seed, stream_handle):
+    _check(_lib().orand_langevin2d_curand_setup(ctypes.byref(params), particles_ptr, states_ptr, curand_seed,
+                                                stream_handle), "orand_langevin2d_curand_setup")
+
+
+def orand_langevin2d_curand_step(params, particles_ptr, states_ptr, stream_handle):
+    _check(_lib().orand_langevin2d_curand_step(ctypes.byref(params), particles_ptr, states_ptr, stream_handle),
+           "orand_langevin2d_curand_step")
+
+
+def particles_tensor(n):
+    """Device storage for n orand_particle_t (5 x 8 bytes each)."""
+    import torch
+
+    return torch.empty((n, 5), dtype=torch.float64, device="cuda")
+
+
+def particle_state(particles):
+    """(x, y, vx, vy) columns of a particle tensor, as a float64 tensor view."""
+    return particles[:, :4]

@@ -132,3 +132,17 @@ def test_ragged_arguments_rejected_on_host(lib):
     assert lib.orand_fill_ragged(None, r.ctypes.data, 1, 16, 64, None) == -1            # no context
     cfg = orand.RaggedConfig(256, 8192, 16, 0)
     assert lib.orand_ragged_set_config(None, ctypes.byref(cfg)) == -1
+
+
+def test_langevin_arguments_rejected_on_host(lib):
+    P = orand.langevin2d_params
+    assert lib.orand_langevin2d_init(None, 16, None) == -1
+    assert lib.orand_langevin2d_step(ctypes.byref(P(0)), None, 1, None) == 0              # empty: no-op
+    assert lib.orand_langevin2d_step(ctypes.byref(P(4, mass=0.0)), 16, 1, None) == -1
+    assert lib.orand_langevin2d_step(ctypes.byref(P(4, dt=-1e-3)), 16, 1, None) == -1
+    assert lib.orand_langevin2d_step(ctypes.byref(P(4, gamma=float("nan"))), 16, 1, None) == -1
+    assert lib.orand_langevin2d_step(ctypes.byref(P(4)), None, 1, None) == -1
+    assert lib.orand_langevin2d_step(ctypes.byref(P(4)), 4, 1, None) == -3                # not 8-byte aligned
+    assert lib.orand_langevin2d_fused(ctypes.byref(P(4)), 16, 2**32 - 5, 10, None) == -2  # counters wrap
+    assert lib.orand_langevin2d_curand_setup(ctypes.byref(P(4)), 16, None, 1984, None) == -1
+    assert lib.orand_langevin2d_curand_state_bytes() >= 48
