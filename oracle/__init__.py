@@ -83,6 +83,12 @@ def lib():
                                  ctypes.c_float, ctypes.c_float, dp, dp]
         L.orc_langevin2d.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_walk3d_ou_forward.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.c_uint32, ctypes.c_float, fp, ctypes.c_float, ctypes.c_float,
+                                            dp, dp, dp, dp]
+        L.orc_walk3d_ou_adjoint.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.c_float, ctypes.c_float, dp, ctypes.c_double, ctypes.c_double,
+                                            dp, dp, dp, dp]
         L.orc_walk3d_init.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, dp]
         L.orc_walk3d_forward.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float, fp,
@@ -347,3 +353,28 @@ def walk3d_adjoint(seed, n, steps, dt, xT, k, P, p_first=0, threads=1):
     dmu = np.sum([p[0] for p in partial], axis=0) if partial else np.zeros(3)
     dsig = float(np.sum([p[1] for p in partial])) if partial else 0.0
     return dmu, dsig, dx0
+
+
+def walk3d_ou_forward(seed, n, steps, K, dt, mu, sigma, kappa, x0=None, p_first=0, want_ckpt=False):
+    """FP64 3D walk with drift mu - kappa x; returns (xT (n,3), ckpt or None, xs (steps+1, n, 3))."""
+    xT = np.zeros((n, 3), np.float64)
+    n_ck = (steps + K - 1) // K if K else 0
+    ck = np.zeros((n_ck, n, 3), np.float64) if want_ckpt else None
+    xs = np.zeros((steps + 1, n, 3), np.float64)
+    mu_a = (ctypes.c_float * 3)(*[float(m) for m in mu])
+    x0c = None if x0 is None else np.ascontiguousarray(x0, np.float64)
+    lib().orc_walk3d_ou_forward(seed, p_first, n, steps, K, dt, mu_a, sigma, kappa,
+                                None if x0c is None else _dp(x0c), _dp(xT), None if ck is None else _dp(ck), _dp(xs))
+    return xT, ck, xs
+
+
+def walk3d_ou_adjoint(seed, n, steps, dt, kappa, xs, k, P, p_first=0):
+    """Stepped adjoint of the OU walk; returns (dmu (3,), dsigma, dkappa, dx0 (n,3))."""
+    xs = np.ascontiguousarray(xs, np.float64)
+    dmu = np.zeros(3, np.float64)
+    ds = np.zeros(1, np.float64)
+    dk = np.zeros(1, np.float64)
+    dx0 = np.zeros((n, 3), np.float64)
+    lib().orc_walk3d_ou_adjoint(seed, p_first, n, steps, dt, kappa, _dp(xs), k, P, _dp(dmu), _dp(ds), _dp(dk),
+                                _dp(dx0))
+    return dmu, float(ds[0]), float(dk[0]), dx0

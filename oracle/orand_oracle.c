@@ -548,3 +548,81 @@ void orc_langevin2d(uint64_t seed, uint64_t p_first, uint64_t n, uint32_t steps,
         state[4 * i + 3] = vy;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * 3D walk with an Ornstein-Uhlenbeck (x-dependent) drift:
+ *   x_{t+1} = x_t + (mu - kappa x_t) dt + sigma sqrt(dt) z_t,
+ * z_t as in orc_walk3d_forward.  kappa = 0 is that walk exactly.  Forward:
+ * ckpt (nullable) receives x_{jK}; xs (nullable) receives every x_t,
+ * t = 0..steps, laid out [t][i][3] (for the adjoint's dL/dkappa).
+ * ---------------------------------------------------------------------- */
+void orc_walk3d_ou_forward(uint64_t seed, uint64_t p_first, uint64_t n, uint32_t steps, uint32_t K, float dt,
+                           const float mu[3], float sigma, float kappa, const double *x0_in, double *xT,
+                           double *ckpt, double *xs)
+{
+    const double ddt = (double)dt;
+    const double sq = sqrt(ddt);
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t key64 = seed ^ (p_first + i);
+        const uint32_t key[2] = {(uint32_t)(key64 & 0xFFFFFFFFull), (uint32_t)(key64 >> 32)};
+        double x[3];
+        if (x0_in) {
+            for (int c = 0; c < 3; ++c) x[c] = x0_in[3 * i + c];
+        } else {
+            orc_walk3d_init(seed, p_first + i, 1, x);
+        }
+        for (uint32_t t = 0; t < steps; ++t) {
+            if (ckpt && K && t % K == 0)
+                for (int c = 0; c < 3; ++c) ckpt[((uint64_t)(t / K) * n + i) * 3 + c] = x[c];
+            if (xs)
+                for (int c = 0; c < 3; ++c) xs[((uint64_t)t * n + i) * 3 + c] = x[c];
+            double z[3];
+            walk3d_noise(key, t + 1u, z);
+            for (int c = 0; c < 3; ++c)
+                x[c] = x[c] + ((double)mu[c] - (double)kappa * x[c]) * ddt + (double)sigma * sq * z[c];
+        }
+        if (xs)
+            for (int c = 0; c < 3; ++c) xs[((uint64_t)steps * n + i) * 3 + c] = x[c];
+        for (int c = 0; c < 3; ++c) xT[3 * i + c] = x[c];
+    }
+}
+
+/* Adjoint of the OU walk, stepped backwards with the stored positions xs
+ * ([t][i][3], from orc_walk3d_ou_forward):
+ *   lambda_T = k x_T / P;  for t = steps-1 .. 0, with lambda = lambda_{t+1}:
+ *     dL/dmu    += lambda dt
+ *     dL/dsigma += lambda . sqrt(dt) z_t
+ *     dL/dkappa += lambda . (-x_t dt)
+ *     lambda_t   = lambda (1 - kappa dt)        (dx_{t+1}/dx_t = (1 - kappa dt) I)
+ *   dL/dx0 = lambda_0.
+ * Sums over the n given particles. */
+void orc_walk3d_ou_adjoint(uint64_t seed, uint64_t p_first, uint64_t n, uint32_t steps, float dt, float kappa,
+                           const double *xs, double k, double P, double *dmu, double *dsigma, double *dkappa,
+                           double *dx0)
+{
+    const double ddt = (double)dt;
+    const double sq = sqrt(ddt);
+    const double decay = 1.0 - (double)kappa * ddt;
+    dmu[0] = dmu[1] = dmu[2] = 0.0;
+    *dsigma = 0.0;
+    *dkappa = 0.0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t key64 = seed ^ (p_first + i);
+        const uint32_t key[2] = {(uint32_t)(key64 & 0xFFFFFFFFull), (uint32_t)(key64 >> 32)};
+        double lam[3];
+        for (int c = 0; c < 3; ++c) lam[c] = k * xs[((uint64_t)steps * n + i) * 3 + c] / P;
+        for (uint32_t tt = steps; tt > 0; --tt) {
+            const uint32_t t = tt - 1u;
+            double z[3];
+            walk3d_noise(key, t + 1u, z);
+            for (int c = 0; c < 3; ++c) {
+                dmu[c] += lam[c] * ddt;
+                *dsigma += lam[c] * sq * z[c];
+                *dkappa += lam[c] * (-xs[((uint64_t)t * n + i) * 3 + c] * ddt);
+                lam[c] *= decay;
+            }
+        }
+        if (dx0)
+            for (int c = 0; c < 3; ++c) dx0[3 * i + c] = lam[c];
+    }
+}

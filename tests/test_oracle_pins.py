@@ -498,3 +498,65 @@ def test_langevin_stationary_velocity_variance(orc):
     var = (dt / 3) / (1 - c * c)
     assert abs(v.var() / var - 1) < 5 * math.sqrt(2 / v.size)
     assert abs(v.mean()) < 5 * math.sqrt(var / v.size)
+
+
+# ------------------------------------------------------ OU drift (kappa) ----
+
+def test_ou_walk_reduces_to_constant_drift_at_kappa_zero(orc):
+    n = 5
+    xT, ck = orc.walk3d_forward(0, n, W3["steps"], W3["K"], W3["dt"], W3["mu"], W3["sigma"], want_ckpt=True)
+    xT2, ck2, xs = orc.walk3d_ou_forward(0, n, W3["steps"], W3["K"], W3["dt"], W3["mu"], W3["sigma"], 0.0,
+                                         want_ckpt=True)
+    assert np.array_equal(xT, xT2) and np.array_equal(ck, ck2) and np.array_equal(xs[-1], xT)
+    dmu, dsig, dx0 = orc.walk3d_adjoint(0, n, W3["steps"], W3["dt"], xT, W3["k"], n)
+    dmu2, dsig2, dk, dx02 = orc.walk3d_ou_adjoint(0, n, W3["steps"], W3["dt"], 0.0, xs, W3["k"], n)
+    assert np.allclose(dmu, dmu2, rtol=1e-14) and dsig == pytest.approx(dsig2, rel=1e-13)
+    assert np.allclose(dx0, dx02, rtol=1e-14)
+    # dL/dkappa at kappa = 0 is -dt sum_t lambda . x_t with constant lambda = k x_T / P.
+    lam = W3["k"] * xT / n
+    assert dk == pytest.approx(-W3["dt"] * float((lam[None] * xs[:-1]).sum()), rel=1e-12)
+
+
+def test_ou_walk_closed_form_mean(orc):
+    # E[x_T] = x0 c^T + (mu / kappa)(1 - c^T), c = 1 - kappa dt: checked on the
+    # deterministic part by setting sigma = 0.
+    n, steps, kappa = 4, 300, 2.0
+    dt = W3["dt"]
+    x0 = orc.walk3d_init(0, n)
+    xT, _, _ = orc.walk3d_ou_forward(0, n, steps, 0, dt, W3["mu"], 0.0, kappa, x0=x0)
+    c = 1 - _f32(kappa) * dt
+    mu = np.array([_f32(m) for m in W3["mu"]])
+    expect = x0 * c ** steps + (mu / _f32(kappa)) * (1 - c ** steps)
+    assert np.allclose(xT, expect, rtol=1e-12, atol=1e-13)
+
+
+def test_ou_adjoint_vs_central_differences(orc):
+    # The loss is quadratic in (x0, mu, sigma) and polynomial in kappa:
+    # central differences are exact for the first three and O(h^2) for kappa.
+    n, steps, K, kappa = 6, 50, 8, 1.5
+    dt = W3["dt"]
+    x0 = orc.walk3d_init(0, n)
+
+    def loss(mu, sigma, kap, x0v):
+        xT, _, _ = orc.walk3d_ou_forward(0, n, steps, K, dt, mu, sigma, kap, x0=x0v)
+        return orc.walk3d_loss(xT, W3["k"], n)
+
+    _, _, xs = orc.walk3d_ou_forward(0, n, steps, K, dt, W3["mu"], W3["sigma"], kappa, x0=x0)
+    dmu, dsig, dk, dx0 = orc.walk3d_ou_adjoint(0, n, steps, dt, kappa, xs, W3["k"], n)
+    h = 1e-3
+    kp, km = _f32(_f32(kappa) + h), _f32(_f32(kappa) - h)
+    fd = (loss(W3["mu"], W3["sigma"], kp, x0) - loss(W3["mu"], W3["sigma"], km, x0)) / (kp - km)
+    assert fd == pytest.approx(dk, rel=1e-5)
+    sp, sm = _f32(_f32(W3["sigma"]) + h), _f32(_f32(W3["sigma"]) - h)
+    fd = (loss(W3["mu"], sp, kappa, x0) - loss(W3["mu"], sm, kappa, x0)) / (sp - sm)
+    assert fd == pytest.approx(dsig, rel=1e-7)
+    for c in range(3):
+        mp, mm = list(W3["mu"]), list(W3["mu"])
+        mp[c], mm[c] = _f32(_f32(mp[c]) + h), _f32(_f32(mm[c]) - h)
+        fd = (loss(mp, W3["sigma"], kappa, x0) - loss(mm, W3["sigma"], kappa, x0)) / (mp[c] - mm[c])
+        assert fd == pytest.approx(dmu[c], rel=1e-7)
+    xp, xm = x0.copy(), x0.copy()
+    xp[2, 1] += h
+    xm[2, 1] -= h
+    fd = (loss(W3["mu"], W3["sigma"], kappa, xp) - loss(W3["mu"], W3["sigma"], kappa, xm)) / (2 * h)
+    assert fd == pytest.approx(dx0[2, 1], rel=1e-7)
