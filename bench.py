@@ -191,9 +191,25 @@ def walk_rows(torch, orand, W, rank):
 
     def run3(sh):
         orand.orand_walk3d_fwd(ctx, prm3, 0, xT.data_ptr(), ck.data_ptr(), loss.data_ptr(), sh)
-        orand.orand_walk3d_bwd(ctx, prm3, xT.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(), dx0.data_ptr(), sh)
+        orand.orand_walk3d_bwd(ctx, prm3, xT.data_ptr(), ck.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(), 0,
+                               dx0.data_ptr(), sh)
 
     rows.append(Row("walk3d/fused_fwd+adjoint", run3, P3 * T, "particle-steps", 5))
+
+    # The same walk with drift mu - kappa x: the adjoint recomputes positions
+    # backwards from the checkpoints and also returns dL/dkappa.
+    co = W.WALK3D_OU
+    prmo = orand.walk3d_params(P3, T, co["dt"], co["mu"], co["sigma"], co["k"], co["seed"], co["ckpt_every"],
+                               p_first=rank * P3, p_total=P3, kappa=co["kappa"])
+    dkap = torch.empty((), dtype=torch.float64, device="cuda")
+    keep["dkap"] = dkap
+
+    def run3ou(sh):
+        orand.orand_walk3d_fwd(ctx, prmo, 0, xT.data_ptr(), ck.data_ptr(), loss.data_ptr(), sh)
+        orand.orand_walk3d_bwd(ctx, prmo, xT.data_ptr(), ck.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(),
+                               dkap.data_ptr(), dx0.data_ptr(), sh)
+
+    rows.append(Row("walk3d/ou_fused_fwd+adjoint", run3ou, P3 * T, "particle-steps", 6))
     return rows, keep
 
 

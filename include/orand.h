@@ -95,7 +95,7 @@ orand_status_t orand_fill(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, u
                           uint64_t n_streams, uint64_t draws_per_stream, void *out, cudaStream_t stream);
 
 /* The word -> value maps alone, applied to caller-provided generator words
- * (Fig. 1's draw helpers; BASELINE's Box-Muller): value j of `dtype` from
+ * (Fig. 1's draw helpers and the Box-Muller normal map): value j of `dtype` from
  * words[j] (u32, FP32 uniform), words[2j], words[2j+1] (FP64 uniform, first
  * high) or the pair words[2(j/2)], words[2(j/2)+1] (FP32 normal, j even the
  * cosine, j odd the sine).  words holds 2*n_values words for FP64,
@@ -144,8 +144,9 @@ typedef struct orand_walk2d_t {
 orand_status_t orand_brownian_walk(const orand_walk2d_t *p, float *pos_out, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
- * Differentiable 3D Brownian walk with constant drift.
- * x_{t+1} = x_t + mu dt + sigma sqrt(dt) z_t, t = 0..steps-1, where z_t are
+ * Differentiable 3D Brownian walk with drift mu - kappa x (kappa = 0: the
+ * constant-drift walk; kappa > 0: Ornstein-Uhlenbeck).
+ * x_{t+1} = x_t + (mu - kappa x_t) dt + sigma sqrt(dt) z_t, t = 0..steps-1, where z_t are
  * the first three Box-Muller normals of the Philox block with counter
  * (0, t+1, 0, 0) and key seed ^ (p_first + i): (z0, z1) from words 0-1,
  * z2 the cosine normal of words 2-3.  x_0 is given, or else
@@ -170,6 +171,8 @@ typedef struct orand_walk3d_t {
     float mu[3];
     float sigma;
     float k;
+    float kappa;          /* mean reversion; 0 = constant drift */
+    uint32_t reserved;    /* must be 0 */
 } orand_walk3d_t;
 
 /* x0 = 2u - 1 from counter 0, as the forward uses when x0 is NULL. */
@@ -182,12 +185,21 @@ orand_status_t orand_walk3d_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
                                 float *ckpt, double *loss, cudaStream_t stream);
 
 /* Adjoint: regenerates every z_t from its (particle, t+1) key instead of
- * reading stored noise.  Writes dL/dmu (3 doubles), dL/dsigma (1 double)
- * and dL/dx0 (n x 3 floats, may be NULL), each scaled by *grad_loss
- * (a device double; NULL means 1).  The drift does not depend on x, so
- * dx_{t+1}/dx_t = I and the adjoint needs only x_T, not the checkpoints. */
-orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
-                                const double *grad_loss, double *dmu, double *dsigma, float *dx0,
+ * reading stored noise.  Writes dL/dmu (3 doubles), dL/dsigma (1 double),
+ * dL/dkappa (1 double, may be NULL) and dL/dx0 (n x 3 floats, may be NULL),
+ * each scaled by *grad_loss (a device double; NULL means 1).
+ * With kappa = 0 and dkappa NULL, dx_{t+1}/dx_t = I: the adjoint needs only
+ * x_T, and ckpt may be NULL.  Otherwise the adjoint lambda_t decays by
+ * (1 - kappa dt) per step, and dL/dkappa = -dt sum_t lambda_{t+1} . x_t needs
+ * every position.  The kernel recomputes x_t backwards in time from the end
+ * of each checkpoint segment:
+ *     x_t = (x_{t+1} - mu dt - sigma sqrt(dt) z_t) / (1 - kappa dt),
+ * so ckpt (from orand_walk3d_fwd, same p) is required and ckpt_every must be
+ * > 0.  A segment of at most ckpt_every steps bounds the growth of rounding
+ * error.  Errors: as the forward, plus INVALID_ARG if a needed ckpt is
+ * missing. */
+orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT, const float *ckpt,
+                                const double *grad_loss, double *dmu, double *dsigma, double *dkappa, float *dx0,
                                 cudaStream_t stream);
 
 /* The adjoint above without a context and without any memory allocation.
@@ -198,7 +210,7 @@ orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
  * latency-sensitive code that cannot take the device-wide synchronisation
  * cudaMalloc/cudaFree imply.
  * Inputs and outputs are exactly those of orand_walk3d_bwd, with the same
- * bits.  The per-block reduction partials live in a fixed 512 KiB array in
+ * bits.  The per-block reduction partials live in a fixed 640 KiB array in
  * the library's device memory, reserved when the library is loaded and held
  * by every device that loads it until the process exits.  That bounds
  * n_particles to at most 4,194,304 (2^22, one 256-thread block per 256
@@ -212,11 +224,12 @@ orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
  * calls that run at the same time on the GPU (other streams or threads)
  * race on it: order them, for example on one stream.
  * Errors: as orand_walk3d_bwd, plus ORAND_ERR_SCRATCH_LIMIT. */
-orand_status_t orand_walk3d_bwd_noalloc(const orand_walk3d_t *p, const float *xT, const double *grad_loss,
-                                        double *dmu, double *dsigma, float *dx0, cudaStream_t stream);
+orand_status_t orand_walk3d_bwd_noalloc(const orand_walk3d_t *p, const float *xT, const float *ckpt,
+                                        const double *grad_loss, double *dmu, double *dsigma, double *dkappa,
+                                        float *dx0, cudaStream_t stream);
 
-/* Plain baseline of the same walk, in the paper's one-launch-per-step
- * pattern (Fig. 1 host loop).  It stores every noise draw: z_store is
+/* Plain baseline of the same walk (kappa must be 0), in the paper's
+ * one-launch-per-step pattern (Fig. 1 host loop).  It stores every noise draw: z_store is
  * steps x n_particles x 3 floats.  It works on x in place, starting from
  * x0 (or the counter-0 init), and accumulates without compensation.  The
  * backward reads z_store back, one launch per step, and keeps its

@@ -60,8 +60,8 @@ _SIGS = {
     "orand_brownian_walk": (_i32, [_vp, _vp, _vp]),
     "orand_walk3d_init": (_i32, [_vp, _vp, _vp]),
     "orand_walk3d_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
-    "orand_walk3d_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
-    "orand_walk3d_bwd_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_walk3d_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_walk3d_bwd_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_langevin2d_init": (_i32, [_vp, _vp, _vp]),
@@ -100,7 +100,7 @@ class Walk3DParams(ctypes.Structure):
     """orand_walk3d_t."""
     _fields_ = [("n_particles", _u64), ("p_first", _u64), ("p_total", _u64), ("seed", _u64),
                 ("steps", _u32), ("ckpt_every", _u32), ("dt", _f32), ("mu", _f32 * 3), ("sigma", _f32),
-                ("k", _f32)]
+                ("k", _f32), ("kappa", _f32), ("reserved", _u32)]
 
 
 class Langevin2DParams(ctypes.Structure):
@@ -111,7 +111,7 @@ class Langevin2DParams(ctypes.Structure):
 
 PARTICLE_BYTES = 40  # orand_particle_t: x, y, vx, vy (double), pid (uint64)
 
-assert ctypes.sizeof(Walk2DParams) == 40 and ctypes.sizeof(Walk3DParams) == 64
+assert ctypes.sizeof(Walk2DParams) == 40 and ctypes.sizeof(Walk3DParams) == 72
 
 
 def _lib():
@@ -264,9 +264,9 @@ def brownian_walk(n_particles, steps, dt=1e-3, D=1.0, seed=0, p_first=0, out=Non
 
 
 def walk3d_params(n_particles, steps, dt=1e-3, mu=(0.1, -0.2, 0.05), sigma=0.5, k=2.0, seed=0,
-                  ckpt_every=64, p_first=0, p_total=0) -> Walk3DParams:
+                  ckpt_every=64, p_first=0, p_total=0, kappa=0.0) -> Walk3DParams:
     return Walk3DParams(n_particles, p_first, p_total, seed & (2**64 - 1), steps, ckpt_every, dt,
-                        (_f32 * 3)(*[float(m) for m in mu]), float(sigma), float(k))
+                        (_f32 * 3)(*[float(m) for m in mu]), float(sigma), float(k), float(kappa), 0)
 
 
 def n_checkpoints(steps, ckpt_every):
@@ -282,15 +282,18 @@ def orand_walk3d_fwd(ctx, params, x0_ptr, xT_ptr, ckpt_ptr, loss_ptr, stream_han
                                    stream_handle), "orand_walk3d_fwd")
 
 
-def orand_walk3d_bwd(ctx, params, xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dx0_ptr, stream_handle):
-    _check(_lib().orand_walk3d_bwd(ctx, ctypes.byref(params), xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr,
-                                   dx0_ptr, stream_handle), "orand_walk3d_bwd")
+def orand_walk3d_bwd(ctx, params, xT_ptr, ckpt_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dkappa_ptr, dx0_ptr,
+                     stream_handle):
+    _check(_lib().orand_walk3d_bwd(ctx, ctypes.byref(params), xT_ptr, ckpt_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr,
+                                   dkappa_ptr, dx0_ptr, stream_handle), "orand_walk3d_bwd")
 
 
-def orand_walk3d_bwd_noalloc(params, xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dx0_ptr, stream_handle):
+def orand_walk3d_bwd_noalloc(params, xT_ptr, ckpt_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dkappa_ptr, dx0_ptr,
+                             stream_handle):
     """The adjoint without a context or any allocation (fixed 2^22-particle scratch)."""
-    _check(_lib().orand_walk3d_bwd_noalloc(ctypes.byref(params), xT_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr,
-                                           dx0_ptr, stream_handle), "orand_walk3d_bwd_noalloc")
+    _check(_lib().orand_walk3d_bwd_noalloc(ctypes.byref(params), xT_ptr, ckpt_ptr, grad_loss_ptr, dmu_ptr,
+                                           dsigma_ptr, dkappa_ptr, dx0_ptr, stream_handle),
+           "orand_walk3d_bwd_noalloc")
 
 
 def orand_walk3d_plain_fwd(ctx, params, x0_ptr, x_ptr, z_ptr, loss_ptr, stream_handle):
@@ -329,54 +332,77 @@ def walk3d_forward(params: Walk3DParams, x0=None, want_ckpt=True, stream=None):
     return xT, ckpt, loss
 
 
-def walk3d_backward(params: Walk3DParams, xT, grad_loss=None, stream=None):
-    """Noise-regenerating adjoint: returns (dmu (3,) f64, dsigma 0-dim f64, dx0 (n,3) f32)."""
+def walk3d_backward(params: Walk3DParams, xT, grad_loss=None, ckpt=None, stream=None):
+    """Noise-regenerating adjoint: returns (dmu (3,) f64, dsigma 0-dim f64, dx0 (n,3) f32).
+    With kappa != 0 the forward's checkpoints are required."""
+    dmu, dsig, _, dx0 = _walk3d_backward(params, xT, grad_loss, ckpt, False, stream)
+    return dmu, dsig, dx0
+
+
+def walk3d_backward_full(params: Walk3DParams, xT, ckpt, grad_loss=None, stream=None):
+    """Adjoint including dL/dkappa: returns (dmu, dsigma, dkappa, dx0); needs the checkpoints."""
+    return _walk3d_backward(params, xT, grad_loss, ckpt, True, stream)
+
+
+def _walk3d_backward(params, xT, grad_loss, ckpt, want_dkappa, stream):
     import torch
 
     dmu = torch.empty(3, dtype=torch.float64, device="cuda")
     dsig = torch.empty((), dtype=torch.float64, device="cuda")
+    dkap = torch.empty((), dtype=torch.float64, device="cuda") if want_dkappa else None
     dx0 = torch.empty_like(xT)
     g = None if grad_loss is None else grad_loss.detach().to(device="cuda", dtype=torch.float64).contiguous()
-    orand_walk3d_bwd(default_context().handle, params, _ptr(xT.contiguous()), _ptr(g), _ptr(dmu), _ptr(dsig),
-                     _ptr(dx0), _stream_handle(stream))
-    return dmu, dsig, dx0
+    ck = None if ckpt is None else ckpt.contiguous()
+    orand_walk3d_bwd(default_context().handle, params, _ptr(xT.contiguous()), _ptr(ck), _ptr(g), _ptr(dmu),
+                     _ptr(dsig), _ptr(dkap), _ptr(dx0), _stream_handle(stream))
+    return dmu, dsig, dkap, dx0
 
 
 def _autograd_function():
     import torch
 
     class BrownianWalk3D(torch.autograd.Function):
-        """loss = BrownianWalk3D.apply(mu, sigma, x0, steps, dt, k, seed, ckpt_every)
+        """loss = BrownianWalk3D.apply(mu, sigma, x0, steps, dt, k, seed, ckpt_every, kappa)
 
-        Forward runs the fused walk (checkpoints every `ckpt_every` steps are
-        kept on the context for inspection via `last_checkpoints`); backward
-        runs the adjoint kernel, which regenerates every noise draw from its
-        (particle, step) key instead of storing it.  mu: (3,) tensor,
-        sigma: 0-dim tensor (either may require grad), x0: (n, 3) CUDA float32.
+        Forward runs the fused walk with drift mu - kappa x.  It writes
+        checkpoints every `ckpt_every` steps (kept for backward and exposed as
+        `last_checkpoints`).  Backward runs the adjoint kernel, which
+        regenerates every noise draw from its (particle, step) key instead of
+        storing it; for kappa it recomputes positions backwards from the
+        checkpoints.  mu: (3,) tensor; sigma and kappa: 0-dim tensors (each
+        may require grad; kappa may be None for 0); x0: (n, 3) CUDA float32.
         """
 
         last_checkpoints = None
 
         @staticmethod
-        def forward(ctx, mu, sigma, x0, steps, dt=1e-3, k=2.0, seed=0, ckpt_every=64):
+        def forward(ctx, mu, sigma, x0, steps, dt=1e-3, k=2.0, seed=0, ckpt_every=64, kappa=None):
             mu_v = [float(v) for v in mu.detach().cpu().tolist()]
+            kap = 0.0 if kappa is None else float(kappa.detach().cpu())
             p = walk3d_params(x0.shape[0], int(steps), float(dt), mu_v, float(sigma.detach().cpu()), float(k),
-                              int(seed), int(ckpt_every))
+                              int(seed), int(ckpt_every), kappa=kap)
             xT, ckpt, loss = walk3d_forward(p, x0=x0, want_ckpt=bool(ckpt_every))
             BrownianWalk3D.last_checkpoints = ckpt
             ctx.params = p
-            ctx.mu_meta = (mu.dtype, mu.device)
-            ctx.sigma_meta = (sigma.dtype, sigma.device)
-            ctx.save_for_backward(xT)
+            ctx.want_dkappa = kappa is not None and kappa.requires_grad
+            ctx.meta = [(t.dtype, t.device) if t is not None else None for t in (mu, sigma, kappa)]
+            if ckpt is None:
+                ctx.save_for_backward(xT)
+            else:
+                ctx.save_for_backward(xT, ckpt)
             return loss
 
         @staticmethod
         def backward(ctx, grad_loss):
-            (xT,) = ctx.saved_tensors
-            dmu, dsig, dx0 = walk3d_backward(ctx.params, xT, grad_loss)
-            return (dmu.to(dtype=ctx.mu_meta[0], device=ctx.mu_meta[1]),
-                    dsig.to(dtype=ctx.sigma_meta[0], device=ctx.sigma_meta[1]), dx0,
-                    None, None, None, None, None)
+            saved = ctx.saved_tensors
+            xT, ckpt = saved[0], (saved[1] if len(saved) > 1 else None)
+            dmu, dsig, dkap, dx0 = _walk3d_backward(ctx.params, xT, grad_loss, ckpt, ctx.want_dkappa, None)
+            (mdt, mdev), (sdt, sdev) = ctx.meta[0], ctx.meta[1]
+            gk = None
+            if ctx.want_dkappa:
+                gk = dkap.to(dtype=ctx.meta[2][0], device=ctx.meta[2][1])
+            return (dmu.to(dtype=mdt, device=mdev), dsig.to(dtype=sdt, device=sdev), dx0,
+                    None, None, None, None, None, gk)
 
     return BrownianWalk3D
 

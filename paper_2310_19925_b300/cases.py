@@ -80,7 +80,8 @@ def main(argv=None):
 
         def fn():
             orand.orand_walk3d_fwd(ctx, prm, 0, xT.data_ptr(), ck.data_ptr(), loss.data_ptr(), sh)
-            orand.orand_walk3d_bwd(ctx, prm, xT.data_ptr(), 0, g.data_ptr(), g.data_ptr() + 24, dx0.data_ptr(), sh)
+            orand.orand_walk3d_bwd(ctx, prm, xT.data_ptr(), ck.data_ptr(), 0, g.data_ptr(), g.data_ptr() + 24, 0,
+                                   dx0.data_ptr(), sh)
 
         ts = timed(torch, fn, args.reps)
         res.update(particles=args.particles, steps=args.steps, ms=statistics.mean(ts),

@@ -19,7 +19,7 @@
 namespace orand_impl {
 
 constexpr int kWalkBlock = 256;
-constexpr int kRedWidth = 4;  // FP64 partial sums per block: loss or (dmu0..2, dsigma)
+constexpr int kRedWidth = 5;  // FP64 partial sums per block: loss, or (dmu0..2, dsigma, dkappa)
 
 // Kahan-compensated x += inc.
 __device__ __forceinline__ void kahan_add(float &x, float &c, float inc)
@@ -102,11 +102,17 @@ __global__ void __launch_bounds__(kWalkBlock) walk2d_kernel(uint64_t n, uint64_t
 struct Walk3dArgs {
     uint64_t n, p_first, seed;
     uint32_t steps, K;
-    float mu_dt[3];   // fl32(mu_c * dt)
-    float sig_sqdt;   // fl32(sigma * sqrt(dt))
-    double k_over_p;  // k / p_total
-    double t_dt;      // steps * dt (FP64, exact product of the FP32 dt)
-    double sqdt;      // sqrt(dt) in FP64
+    float mu_dt[3];     // fl32(mu_c * dt)
+    float sig_sqdt;     // fl32(sigma * sqrt(dt))
+    float kappa_dt;     // fl32(kappa * dt)
+    float decay_f;      // fl32(1 - kappa dt): lambda_t = lambda_{t+1} * decay
+    float inv_decay_f;  // fl32(1 / (1 - kappa dt)): reverse-time position recompute
+    double k_over_p;    // k / p_total
+    double t_dt;        // steps * dt (FP64, exact product of the FP32 dt)
+    double sqdt;        // sqrt(dt) in FP64
+    double dt;          // dt in FP64
+    double decay_K;     // (1 - kappa dt)^K: lambda across one full checkpoint segment
+    double decay_last;  // (1 - kappa dt)^(steps - (nseg - 1) K): the last, possibly short, segment
 };
 
 __device__ __forceinline__ void walk3d_normals(const orand::PhiloxKeys &keys, uint32_t t_counter, float z[3])
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_fwd_kernel(Walk3dArgs a, co
                                                                double *__restrict__ partials)
 {
     const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
-    double loss[kRedWidth] = {0.0, 0.0, 0.0, 0.0};
+    double loss[kRedWidth] = {};
     if (i < a.n) {
         const orand::PhiloxKeys keys(a.seed ^ (a.p_first + i));
         float x[3], c[3] = {0.f, 0.f, 0.f};
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_fwd_kernel(Walk3dArgs a, co
             float z[3];
             walk3d_scaled_normals(keys, t + 1u, a.sig_sqdt, z);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], z[q] + a.mu_dt[q]);
+            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], fmaf(-a.kappa_dt, x[q], z[q] + a.mu_dt[q]));
         }
         xT[3 * i] = x[0];
         xT[3 * i + 1] = x[1];
@@ -193,34 +199,86 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_fwd_kernel(Walk3dArgs a, co
     if (partials) block_reduce_store<kRedWidth>(loss, partials);
 }
 
-// Adjoint: lambda = k x_T / p_total * g is constant in time (constant drift).
-// dL/dmu_c = lambda_c * steps * dt, dL/dsigma = sum_c lambda_c sqrt(dt) sum_t z_t,c,
-// with every z_t regenerated from its key, walking time backwards.
+// Adjoint of the walk and the loss, regenerating every z_t from its key and
+// walking time backwards.  lambda_T = k x_T / p_total * g.
+//   OU = false (kappa = 0, dL/dkappa not wanted): lambda is constant, so
+//     dL/dmu_c = lambda_c T dt and dL/dsigma = sum_c lambda_c sqrt(dt) sum_t z_t,c.
+//   OU = true: per checkpoint segment, newest first, starting from the
+//     segment's end position (the next checkpoint, or x_T), each step t-1 -> t
+//     (noise counter t) adds lambda_t dt to dL/dmu, lambda_t . sqrt(dt) z_{t-1}
+//     to dL/dsigma and lambda_t . (-x_{t-1} dt) to dL/dkappa.  Then it
+//     recomputes x_{t-1} = (x_t - mu dt - sigma sqrt(dt) z_{t-1}) / (1 - kappa dt)
+//     and sets lambda_{t-1} = lambda_t (1 - kappa dt).  lambda and the sums run
+//     in FP32 within a segment (at most K steps) and are re-anchored in FP64
+//     between segments.
+template <bool OU>
 __global__ void __launch_bounds__(kWalkBlock) walk3d_bwd_kernel(Walk3dArgs a, const float *__restrict__ xT,
+                                                               const float *__restrict__ ckpt,
                                                                const double *__restrict__ grad_loss,
                                                                float *__restrict__ dx0,
                                                                double *__restrict__ partials)
 {
     const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
-    double g[kRedWidth] = {0.0, 0.0, 0.0, 0.0};
+    double g[kRedWidth] = {};
     if (i < a.n) {
         const double gl = grad_loss ? *grad_loss : 1.0;
         const orand::PhiloxKeys keys(a.seed ^ (a.p_first + i));
         double lam[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) lam[q] = a.k_over_p * (double)xT[3 * i + q] * gl;
-        float S[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
-        for (uint32_t tt = a.steps; tt > 0; --tt) {
-            float z[3];
-            walk3d_normals(keys, tt, z);   // z_{tt-1} uses counter tt
+        if constexpr (!OU) {
+            float S[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+            for (uint32_t tt = a.steps; tt > 0; --tt) {
+                float z[3];
+                walk3d_normals(keys, tt, z);   // z_{tt-1} uses counter tt
 #pragma unroll
-            for (int q = 0; q < 3; ++q) kahan_add(S[q], c[q], z[q]);
+                for (int q = 0; q < 3; ++q) kahan_add(S[q], c[q], z[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                g[q] = lam[q] * a.t_dt;
+                g[3] += lam[q] * a.sqdt * (double)S[q];
+            }
+        } else {
+            float x[3] = {xT[3 * i], xT[3 * i + 1], xT[3 * i + 2]};
+            const uint32_t nseg = (a.steps + a.K - 1) / a.K;
+            for (uint32_t jj = nseg; jj > 0; --jj) {
+                const uint32_t t0 = (jj - 1) * a.K;
+                const uint32_t t1 = min(a.steps, t0 + a.K);
+                if (jj < nseg) {   // segment end x_{jj K} is checkpoint jj
+                    const float *ck = ckpt + ((size_t)jj * a.n + i) * 3;
+                    x[0] = ck[0];
+                    x[1] = ck[1];
+                    x[2] = ck[2];
+                }
+                float lf[3] = {(float)lam[0], (float)lam[1], (float)lam[2]};
+                float amu[3] = {0.f, 0.f, 0.f}, asig = 0.f, akap = 0.f;
+                for (uint32_t t = t1; t > t0; --t) {
+                    float z[3];
+                    walk3d_normals(keys, t, z);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        amu[q] += lf[q];
+                        asig = fmaf(lf[q], z[q], asig);
+                        const float xp = (x[q] - fmaf(a.sig_sqdt, z[q], a.mu_dt[q])) * a.inv_decay_f;
+                        akap = fmaf(lf[q], xp, akap);
+                        x[q] = xp;
+                        lf[q] *= a.decay_f;
+                    }
+                }
+                const double seg_decay = (jj == nseg) ? a.decay_last : a.decay_K;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    g[q] += (double)amu[q] * a.dt;
+                    lam[q] *= seg_decay;
+                }
+                g[3] += (double)asig * a.sqdt;
+                g[4] -= (double)akap * a.dt;
+            }
         }
+        if (dx0) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            g[q] = lam[q] * a.t_dt;
-            g[3] += lam[q] * a.sqdt * (double)S[q];
-            if (dx0) dx0[3 * i + q] = (float)lam[q];
+            for (int q = 0; q < 3; ++q) dx0[3 * i + q] = (float)lam[q];
         }
     }
     block_reduce_store<kRedWidth>(g, partials);
@@ -258,7 +316,7 @@ __global__ void __launch_bounds__(kWalkBlock) plain_step_kernel(Walk3dArgs a, ui
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         z_t[3 * i + q] = z[q];
-        x[3 * i + q] = x[3 * i + q] + fmaf(a.sig_sqdt, z[q], a.mu_dt[q]);
+        x[3 * i + q] = x[3 * i + q] + fmaf(-a.kappa_dt, x[3 * i + q], fmaf(a.sig_sqdt, z[q], a.mu_dt[q]));
     }
 }
 
@@ -266,7 +324,7 @@ __global__ void __launch_bounds__(kWalkBlock) plain_loss_kernel(Walk3dArgs a, co
                                                                double *__restrict__ partials)
 {
     const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
-    double v[kRedWidth] = {0.0, 0.0, 0.0, 0.0};
+    double v[kRedWidth] = {};
     if (i < a.n) {
         const double r2 = (double)x[3 * i] * x[3 * i] + (double)x[3 * i + 1] * x[3 * i + 1] +
                           (double)x[3 * i + 2] * x[3 * i + 2];
@@ -290,7 +348,7 @@ __global__ void __launch_bounds__(kWalkBlock) plain_bwd_final_kernel(Walk3dArgs 
                                                                     double *__restrict__ partials)
 {
     const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
-    double g[kRedWidth] = {0.0, 0.0, 0.0, 0.0};
+    double g[kRedWidth] = {};
     if (i < a.n) {
         const double gl = grad_loss ? *grad_loss : 1.0;
         for (int q = 0; q < 3; ++q) {
@@ -316,8 +374,9 @@ static orand_status_t walk3d_args(const orand_walk3d_t *p, Walk3dArgs *a)
 {
     if (p == nullptr) return ORAND_ERR_INVALID_ARG;
     if (!finite_nonneg(p->dt) || !finite_nonneg(p->sigma) || !isfinite(p->k) || !isfinite(p->mu[0]) ||
-        !isfinite(p->mu[1]) || !isfinite(p->mu[2]))
+        !isfinite(p->mu[1]) || !isfinite(p->mu[2]) || !isfinite(p->kappa) || p->reserved != 0)
         return ORAND_ERR_INVALID_ARG;
+    if (!(1.0 - (double)p->kappa * (double)p->dt > 0.0)) return ORAND_ERR_INVALID_ARG;  // decay must stay positive
     if (p->p_first + p->n_particles < p->p_first) return ORAND_ERR_OVERFLOW;
     if (!walk_grid_ok(p->n_particles)) return ORAND_ERR_OVERFLOW;
     if (p->steps == UINT32_MAX) return ORAND_ERR_OVERFLOW;  // counters t + 1 must fit 32 bits
@@ -333,6 +392,14 @@ static orand_status_t walk3d_args(const orand_walk3d_t *p, Walk3dArgs *a)
     a->k_over_p = P > 0 ? (double)p->k / P : 0.0;
     a->t_dt = (double)p->steps * dt;
     a->sqdt = sqrt(dt);
+    a->dt = dt;
+    const double decay = 1.0 - (double)p->kappa * dt;
+    a->kappa_dt = (float)((double)p->kappa * dt);
+    a->decay_f = (float)decay;
+    a->inv_decay_f = (float)(1.0 / decay);
+    const uint32_t nseg = a->K ? (a->steps + a->K - 1) / a->K : 0;
+    a->decay_K = a->K ? pow(decay, (double)a->K) : 1.0;
+    a->decay_last = nseg ? pow(decay, (double)(a->steps - (nseg - 1) * a->K)) : 1.0;
     return ORAND_OK;
 }
 
@@ -342,6 +409,52 @@ static orand_status_t check_ptr(const void *ptr, size_t align)
 {
     if (ptr == nullptr) return ORAND_ERR_INVALID_ARG;
     return ((uintptr_t)ptr % align) ? ORAND_ERR_ALIGNMENT : ORAND_OK;
+}
+
+// Argument checks of the adjoint shared by both entry points.  With
+// kappa != 0 or dL/dkappa wanted, the checkpoints are needed (ckpt_every > 0).
+static orand_status_t bwd_validate(const Walk3dArgs &a, const orand_walk3d_t *p, const float *xT,
+                                   const float *ckpt, const double *grad_loss, double *dmu, double *dsigma,
+                                   double *dkappa, float *dx0)
+{
+    orand_status_t st;
+    if ((st = check_ptr(dmu, 8)) != ORAND_OK || (st = check_ptr(dsigma, 8)) != ORAND_OK) return st;
+    if (dkappa && ((uintptr_t)dkappa % 8)) return ORAND_ERR_ALIGNMENT;
+    if (a.n == 0) return ORAND_OK;
+    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
+    if (dx0 && ((uintptr_t)dx0 % 4)) return ORAND_ERR_ALIGNMENT;
+    if (grad_loss && ((uintptr_t)grad_loss % 8)) return ORAND_ERR_ALIGNMENT;
+    const bool ou = p->kappa != 0.0f || dkappa != nullptr;
+    if (ou && a.steps > 0) {
+        if (a.K == 0) return ORAND_ERR_INVALID_ARG;
+        if (a.steps > a.K && (st = check_ptr(ckpt, 4)) != ORAND_OK) return st;
+    }
+    return ORAND_OK;
+}
+
+static orand_status_t bwd_zero(double *dmu, double *dsigma, double *dkappa, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(dmu, 0, 3 * sizeof(double), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dsigma, 0, sizeof(double), stream);
+    if (e == cudaSuccess && dkappa) e = cudaMemsetAsync(dkappa, 0, sizeof(double), stream);
+    return cuda_status(e);
+}
+
+// Adjoint kernel plus the fixed-order reductions of its FP64 partials.
+static orand_status_t bwd_launch(const Walk3dArgs &a, const orand_walk3d_t *p, const float *xT, const float *ckpt,
+                                 const double *grad_loss, double *dmu, double *dsigma, double *dkappa, float *dx0,
+                                 double *partials, cudaStream_t stream)
+{
+    const bool ou = p->kappa != 0.0f || dkappa != nullptr;
+    const unsigned grid = walk_grid(a.n);
+    if (ou) walk3d_bwd_kernel<true><<<grid, kWalkBlock, 0, stream>>>(a, xT, ckpt, grad_loss, dx0, partials);
+    else walk3d_bwd_kernel<false><<<grid, kWalkBlock, 0, stream>>>(a, xT, ckpt, grad_loss, dx0, partials);
+    orand_status_t st = launch_status();
+    if (st != ORAND_OK) return st;
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
+    if (dkappa) reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 4, grid, 1.0, nullptr, dkappa, 1);
+    return launch_status();
 }
 
 }  // namespace orand_impl
@@ -409,32 +522,19 @@ orand_status_t orand_walk3d_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
     return launch_status();
 }
 
-orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
-                                const double *grad_loss, double *dmu, double *dsigma, float *dx0,
+orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT, const float *ckpt,
+                                const double *grad_loss, double *dmu, double *dsigma, double *dkappa, float *dx0,
                                 cudaStream_t stream)
 {
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
     if ((st = ctx_check(ctx)) != ORAND_OK) return st;
-    if ((st = check_ptr(dmu, 8)) != ORAND_OK || (st = check_ptr(dsigma, 8)) != ORAND_OK) return st;
-    if (a.n == 0) {
-        cudaError_t e = cudaMemsetAsync(dmu, 0, 3 * sizeof(double), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(dsigma, 0, sizeof(double), stream);
-        return cuda_status(e);
-    }
-    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
-    if (dx0 && ((uintptr_t)dx0 % 4)) return ORAND_ERR_ALIGNMENT;
-    if (grad_loss && ((uintptr_t)grad_loss % 8)) return ORAND_ERR_ALIGNMENT;
-    const unsigned grid = walk_grid(a.n);
+    if ((st = bwd_validate(a, p, xT, ckpt, grad_loss, dmu, dsigma, dkappa, dx0)) != ORAND_OK) return st;
+    if (a.n == 0) return bwd_zero(dmu, dsigma, dkappa, stream);
     void *scr = nullptr;
-    if ((st = ctx_scratch(ctx, (size_t)grid * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
-    double *partials = (double *)scr;
-    walk3d_bwd_kernel<<<grid, kWalkBlock, 0, stream>>>(a, xT, grad_loss, dx0, partials);
-    if ((st = launch_status()) != ORAND_OK) return st;
-    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
-    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
-    return launch_status();
+    if ((st = ctx_scratch(ctx, (size_t)walk_grid(a.n) * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
+    return bwd_launch(a, p, xT, ckpt, grad_loss, dmu, dsigma, dkappa, dx0, (double *)scr, stream);
 }
 
 orand_status_t orand_walk3d_plain_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *x,
@@ -443,6 +543,7 @@ orand_status_t orand_walk3d_plain_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, 
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
+    if (p->kappa != 0.0f) return ORAND_ERR_INVALID_ARG;  // the baseline is the constant-drift walk
     if ((st = ctx_check(ctx)) != ORAND_OK) return st;
     if (a.n == 0) return ORAND_OK;
     if ((st = check_ptr(x, 4)) != ORAND_OK) return st;
@@ -468,6 +569,7 @@ orand_status_t orand_walk3d_plain_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, 
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
+    if (p->kappa != 0.0f) return ORAND_ERR_INVALID_ARG;
     if ((st = ctx_check(ctx)) != ORAND_OK) return st;
     if ((st = check_ptr(dmu, 8)) != ORAND_OK || (st = check_ptr(dsigma, 8)) != ORAND_OK) return st;
     if (a.n == 0) {
@@ -507,7 +609,7 @@ namespace orand_impl {
 constexpr uint64_t kNoAllocMaxParticles = 1ull << 22;
 constexpr unsigned kNoAllocMaxBlocks = (unsigned)(kNoAllocMaxParticles / kWalkBlock);  // 16384
 
-// 16384 blocks x 4 FP64 partials = 512 KiB, resident on every device that
+// 16384 blocks x 5 FP64 partials = 640 KiB, resident on every device that
 // loads the library.
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * kRedWidth];
 
@@ -538,33 +640,21 @@ static orand_status_t noalloc_partials(double **out)
 
 }  // namespace orand_impl
 
-extern "C" orand_status_t orand_walk3d_bwd_noalloc(const orand_walk3d_t *p, const float *xT,
+extern "C" orand_status_t orand_walk3d_bwd_noalloc(const orand_walk3d_t *p, const float *xT, const float *ckpt,
                                                    const double *grad_loss, double *dmu, double *dsigma,
-                                                   float *dx0, cudaStream_t stream)
+                                                   double *dkappa, float *dx0, cudaStream_t stream)
 {
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
     if (a.n > kNoAllocMaxParticles) return ORAND_ERR_SCRATCH_LIMIT;
-    if ((st = check_ptr(dmu, 8)) != ORAND_OK || (st = check_ptr(dsigma, 8)) != ORAND_OK) return st;
-    if (a.n == 0) {
-        cudaError_t e = cudaMemsetAsync(dmu, 0, 3 * sizeof(double), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(dsigma, 0, sizeof(double), stream);
-        return cuda_status(e);
-    }
-    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
-    if (dx0 && ((uintptr_t)dx0 % 4)) return ORAND_ERR_ALIGNMENT;
-    if (grad_loss && ((uintptr_t)grad_loss % 8)) return ORAND_ERR_ALIGNMENT;
+    if ((st = bwd_validate(a, p, xT, ckpt, grad_loss, dmu, dsigma, dkappa, dx0)) != ORAND_OK) return st;
+    if (a.n == 0) return bwd_zero(dmu, dsigma, dkappa, stream);
     DeviceInfo info;
     if ((st = current_device(&info)) != ORAND_OK) return st;
     double *partials = nullptr;
     if ((st = noalloc_partials(&partials)) != ORAND_OK) return st;
-    // Every partial the reduction reads (blocks 0 .. grid-1) is written by
+    // Every partial the reductions read (blocks 0 .. grid-1) is written by
     // this call's adjoint kernel first: no clearing needed.
-    const unsigned grid = walk_grid(a.n);
-    walk3d_bwd_kernel<<<grid, kWalkBlock, 0, stream>>>(a, xT, grad_loss, dx0, partials);
-    if ((st = launch_status()) != ORAND_OK) return st;
-    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
-    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
-    return launch_status();
+    return bwd_launch(a, p, xT, ckpt, grad_loss, dmu, dsigma, dkappa, dx0, partials, stream);
 }

@@ -19,6 +19,9 @@ Workloads (all synthetic; the paper has no dataset):
   * WALK3D       -- 2^22 particles, 4096 steps, dt = 1e-3,
                     mu = (0.1, -0.2, 0.05), sigma = 0.5, k = 2, checkpoint
                     every 64 steps.
+  * WALK3D_OU    -- the same walk with Ornstein-Uhlenbeck drift
+                    mu - kappa x, kappa = 1 (the checkpoints carry the
+                    adjoint's reverse-time recompute).
 """
 from __future__ import annotations
 
@@ -35,6 +38,7 @@ FILL_LARGE = dict(seed=0x5EED, counter=0, n_streams=1 << 24, dps=16)
 WALK2D = dict(n_particles=1 << 24, steps=10_000, dt=1e-3, D=1.0, seed=0)
 WALK3D = dict(n_particles=1 << 22, steps=4096, dt=1e-3, mu=(0.1, -0.2, 0.05), sigma=0.5, k=2.0,
               ckpt_every=64, seed=0)
+WALK3D_OU = dict(WALK3D, kappa=1.0)
 RAGGED = dict(n_requests=100_000, max_log2_len=20, list_seed=20231030)
 
 # Layout of one ragged request record (matches the C struct orand_request_t).

@@ -223,3 +223,88 @@ def test_walk3d_full_workload(torch_cuda, orc):
     assert (lp - lm) / (sp - sm) == pytest.approx(dsig.item(), rel=GRAD_TOL)
     del xT, ck, dx0
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------- 3D, OU drift mu - kappa x ----
+
+def _pou(n, steps, K, kappa, p_first=0, p_total=0, seed=0):
+    return orand.walk3d_params(n, steps, dt=1e-3, mu=MU, sigma=0.5, k=2.0, seed=seed, ckpt_every=K,
+                               p_first=p_first, p_total=p_total, kappa=kappa)
+
+
+@pytest.mark.parametrize("n,steps,K,kappa", [(777, 200, 16, 1.5), (300, 203, 16, 1.5), (513, 97, 8, 20.0),
+                                             (129, 64, 64, -3.0), (1, 1, 1, 0.5), (256, 150, 32, 0.0)])
+def test_walk3d_ou_forward_and_adjoint(torch_cuda, orc, n, steps, K, kappa):
+    """Fused OU forward and the checkpointed reverse-time adjoint against the
+    FP64 oracle: positions, checkpoints, loss, dmu, dsigma, dkappa and dx0.
+    Covers a short last segment (203 = 12 x 16 + 11), a strongly contracting
+    drift (kappa dt = 0.02), an expanding one (kappa < 0), one segment, one
+    step, and kappa = 0 with dL/dkappa requested."""
+    torch = torch_cuda
+    p = _pou(n, steps, K, kappa, p_first=5, p_total=3 * n)
+    xT, ck, loss = orand.walk3d_forward(p)
+    g = torch.tensor(-1.25, dtype=torch.float64, device="cuda")
+    dmu, dsig, dkap, dx0 = orand.walk3d_backward_full(p, xT, ck, g)
+    torch.cuda.synchronize()
+    dt32 = _f32(1e-3)
+    oxT, ock, xs = orc.walk3d_ou_forward(0, n, steps, K, dt32, MU, 0.5, _f32(kappa), p_first=5, want_ckpt=True)
+    pos_close(to_numpy(xT), oxT)
+    pos_close(to_numpy(ck), ock)
+    assert loss.item() == pytest.approx(orc.walk3d_loss(oxT, 2.0, 3 * n), rel=GRAD_TOL)
+    odmu, odsig, odk, odx0 = orc.walk3d_ou_adjoint(0, n, steps, dt32, _f32(kappa), xs, 2.0, 3 * n, p_first=5)
+    assert np.allclose(to_numpy(dmu), -1.25 * odmu, rtol=GRAD_TOL, atol=0)
+    assert dsig.item() == pytest.approx(-1.25 * odsig, rel=GRAD_TOL)
+    assert dkap.item() == pytest.approx(-1.25 * odk, rel=GRAD_TOL)
+    # dx0 = g k x_T (1 - kappa dt)^T / P inherits the position error absolutely:
+    # where x_T is near 0 the relative bar does not apply, the propagated one does.
+    np.testing.assert_allclose(to_numpy(dx0), -1.25 * odx0, rtol=GRAD_TOL, atol=1.25 * 2.0 / (3 * n) * POS_TOL)
+    # Without dkappa the same entry point gives the same dmu, dsigma, dx0.
+    if kappa != 0.0:
+        dmu2, dsig2, dx02 = orand.walk3d_backward(p, xT, g, ckpt=ck)
+        assert torch.equal(dmu2, dmu) and dsig2.item() == dsig.item() and torch.equal(dx02, dx0)
+
+
+def test_walk3d_ou_argument_checks(torch_cuda):
+    """The kappa != 0 adjoint needs checkpoints; 1 - kappa dt must stay positive."""
+    torch = torch_cuda
+    p = _pou(64, 40, 8, 2.0)
+    xT, ck, _ = orand.walk3d_forward(p)
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        orand.walk3d_backward(p, xT)  # no checkpoints
+    p0 = _pou(64, 40, 0, 2.0)
+    xT0, ck0, _ = orand.walk3d_forward(p0)  # the forward alone needs no checkpoint interval
+    assert ck0 is None
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        orand.walk3d_backward(p0, xT0)  # the adjoint does
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        orand.walk3d_forward(_pou(64, 40, 8, 1000.0))  # kappa dt = 1
+    torch.cuda.synchronize()
+
+
+def test_walk3d_ou_autograd_and_central_differences(torch_cuda, orc):
+    """kappa through BrownianWalk3D: its gradient matches the oracle adjoint
+    and central differences of the GPU forward in kappa."""
+    torch = torch_cuda
+    n, steps, K = 4096, 256, 32
+    BW = orand.BrownianWalk3D()
+    p = _pou(n, steps, K, 2.5)
+    x0 = orand.walk3d_init(p).requires_grad_(True)
+    mu = torch.tensor(MU, dtype=torch.float32, requires_grad=True)
+    sigma = torch.tensor(0.5, dtype=torch.float32, requires_grad=True)
+    kappa = torch.tensor(2.5, dtype=torch.float32, requires_grad=True)
+    loss = BW.apply(mu, sigma, x0, steps, 1e-3, 2.0, 0, K, kappa)
+    loss.backward()
+    dt32 = _f32(1e-3)
+    oxT, _, xs = orc.walk3d_ou_forward(0, n, steps, K, dt32, MU, 0.5, 2.5)
+    odmu, odsig, odk, odx0 = orc.walk3d_ou_adjoint(0, n, steps, dt32, 2.5, xs, 2.0, n)
+    assert loss.item() == pytest.approx(orc.walk3d_loss(oxT, 2.0, n), rel=1e-6)
+    assert np.allclose(mu.grad.numpy(), odmu, rtol=GRAD_TOL)
+    assert sigma.grad.item() == pytest.approx(odsig, rel=GRAD_TOL)
+    assert kappa.grad.item() == pytest.approx(odk, rel=GRAD_TOL)
+    np.testing.assert_allclose(to_numpy(x0.grad), odx0, rtol=GRAD_TOL, atol=2.0 / n * POS_TOL)
+    h = 1e-2
+    with torch.no_grad():
+        lp = BW.apply(mu, sigma, x0, steps, 1e-3, 2.0, 0, K, kappa + h).item()
+        lm = BW.apply(mu, sigma, x0, steps, 1e-3, 2.0, 0, K, kappa - h).item()
+    kp, km = _f32(_f32(2.5) + h), _f32(_f32(2.5) - h)
+    assert (lp - lm) / (kp - km) == pytest.approx(kappa.grad.item(), rel=GRAD_TOL)

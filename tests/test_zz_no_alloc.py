@@ -25,7 +25,7 @@ MAX_PARTICLES = 1 << 22
 def test_size_limit_is_refused_on_the_host():
     lib = orand._lib()
     p = orand.walk3d_params(MAX_PARTICLES + 1, 8)
-    assert lib.orand_walk3d_bwd_noalloc(ctypes.byref(p), 16, None, 16, 16, None, None) == -8
+    assert lib.orand_walk3d_bwd_noalloc(ctypes.byref(p), 16, None, None, 16, 16, None, None, None) == -8
     assert "ORAND_ERR_SCRATCH_LIMIT" in lib.orand_status_string(-8).decode()
 
 
@@ -47,9 +47,32 @@ def test_noalloc_adjoint_matches_context_adjoint_on_consecutive_calls():
         dmu = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
         dsig = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
         dx0 = torch.full_like(xT, float("nan"))
-        orand.orand_walk3d_bwd_noalloc(p, xT.data_ptr(), gl.data_ptr(), dmu.data_ptr(), dsig.data_ptr(),
+        orand.orand_walk3d_bwd_noalloc(p, xT.data_ptr(), 0, gl.data_ptr(), dmu.data_ptr(), dsig.data_ptr(), 0,
                                        dx0.data_ptr(), sh)
         torch.cuda.synchronize()
         np.testing.assert_allclose(dmu.cpu().numpy(), ref_dmu.cpu().numpy(), rtol=GRAD_TOL)
         assert dsig.item() == pytest.approx(ref_dsig.item(), rel=GRAD_TOL)
         torch.testing.assert_close(dx0, ref_dx0, rtol=GRAD_TOL, atol=0.0)
+
+
+@pytest.mark.gpu
+def test_noalloc_adjoint_with_ou_drift_and_dkappa():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sh = torch.cuda.current_stream().cuda_stream
+    p = orand.walk3d_params(5000, 100, ckpt_every=16, kappa=3.0)
+    xT, ck, _ = orand.walk3d_forward(p)
+    ref_dmu, ref_dsig, ref_dk, ref_dx0 = orand.walk3d_backward_full(p, xT, ck)
+    dmu = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    dsig = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
+    dk = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
+    dx0 = torch.full_like(xT, float("nan"))
+    orand.orand_walk3d_bwd_noalloc(p, xT.data_ptr(), ck.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(),
+                                   dk.data_ptr(), dx0.data_ptr(), sh)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(dmu.cpu().numpy(), ref_dmu.cpu().numpy(), rtol=GRAD_TOL)
+    assert dsig.item() == pytest.approx(ref_dsig.item(), rel=GRAD_TOL)
+    assert dk.item() == pytest.approx(ref_dk.item(), rel=GRAD_TOL)
+    torch.testing.assert_close(dx0, ref_dx0, rtol=GRAD_TOL, atol=0.0)
