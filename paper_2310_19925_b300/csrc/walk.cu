@@ -6,7 +6,7 @@
 // Fused kernels keep each particle's position and its Philox round keys in
 // registers for the whole walk.  A step is one Philox block, keyed by the
 // particle id with counter (0, t, 0, 0), followed by Box-Muller in FP32 and
-// a compensated update.  Only the start and end touch HBM.  The cost is
+// a compensated position update.  Only the start and end touch HBM.  The cost is
 // integer- and FP-pipe work per step, not bytes.
 #include <math.h>
 
@@ -76,25 +76,65 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 
 // ------------------------------------------------------------------ 2D walk
 
-__global__ void __launch_bounds__(kWalkBlock) walk2d_kernel(uint64_t n, uint64_t p_first, uint64_t seed,
-                                                           uint32_t steps, float s, float2 *__restrict__ out)
-{
-    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
-    if (i >= n) return;
-    const orand::PhiloxKeys keys(seed ^ (p_first + i));
-    uint4 w = keys.block(0u, 0u);
-    float x = orand::u01_f32(w.x), y = orand::u01_f32(w.y);
-    float cx = 0.f, cy = 0.f;
-    for (uint32_t t = 1; t <= steps; ++t) {
-        w = keys.block(0u, t);
-        // s * (r cos, r sin) with the step scale folded into the radius.
-        const float rs = s * orand::bm_radius(w.x);
-        float c, sn;
-        orand::bm_cos_sin(w.y, &c, &sn);
-        kahan_add(x, cx, rs * c);
-        kahan_add(y, cy, rs * sn);
+// The 2D kernel is bound by instruction issue (about 110 operations per
+// particle-step, nearly all of them the Philox rounds and Box-Muller).  Two
+// particles per thread give the schedulers two independent dependency
+// chains; the position sum is compensated per block of kSumBlock steps
+// (plain FMA sums inside a block, a Kahan add of each block sum), which
+// saves the per-step compensation while keeping the rounding error of the
+// whole walk at the level of one FP32 rounding per block sum.
+constexpr int kWalk2dBlock = 128;
+constexpr int kWalk2dPerThread = 2;
+constexpr uint32_t kSumBlock = 16;
+
+struct Walk2dLane {
+    orand::PhiloxKeys keys;
+    float x, y, cx, cy;
+    __device__ __forceinline__ explicit Walk2dLane(uint64_t key64) : keys(key64), cx(0.f), cy(0.f)
+    {
+        const uint4 w = keys.block(0u, 0u);
+        x = orand::u01_f32(w.x);
+        y = orand::u01_f32(w.y);
     }
-    out[i] = make_float2(x, y);
+};
+
+// Block b covers particles [b * 256, (b + 1) * 256): thread x owns x and x + 128.
+__global__ void __launch_bounds__(kWalk2dBlock) walk2d_kernel(uint64_t n, uint64_t p_first, uint64_t seed,
+                                                             uint32_t steps, float s, float2 *__restrict__ out)
+{
+    const uint64_t base = (uint64_t)blockIdx.x * (kWalk2dBlock * kWalk2dPerThread) + threadIdx.x;
+    Walk2dLane L[kWalk2dPerThread] = {Walk2dLane(seed ^ (p_first + base)),
+                                      Walk2dLane(seed ^ (p_first + base + kWalk2dBlock))};
+    // t runs 1..steps in blocks of kSumBlock; `done` counts steps taken so
+    // the loop cannot wrap when steps is near 2^32.
+    for (uint32_t done = 0; done < steps;) {
+        const uint32_t len = min(kSumBlock, steps - done);
+        float sx[kWalk2dPerThread] = {0.f, 0.f}, sy[kWalk2dPerThread] = {0.f, 0.f};
+        for (uint32_t k = 1; k <= len; ++k) {
+            const uint32_t t = done + k;
+#pragma unroll
+            for (int j = 0; j < kWalk2dPerThread; ++j) {
+                const uint4 w = L[j].keys.block(0u, t);
+                // s * (r cos, r sin) with the step scale folded into the radius.
+                const float rs = s * orand::bm_radius(w.x);
+                float c, sn;
+                orand::bm_cos_sin(w.y, &c, &sn);
+                sx[j] = fmaf(rs, c, sx[j]);
+                sy[j] = fmaf(rs, sn, sy[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kWalk2dPerThread; ++j) {
+            kahan_add(L[j].x, L[j].cx, sx[j]);
+            kahan_add(L[j].y, L[j].cy, sy[j]);
+        }
+        done += len;
+    }
+#pragma unroll
+    for (int j = 0; j < kWalk2dPerThread; ++j) {
+        const uint64_t i = base + (uint64_t)j * kWalk2dBlock;
+        if (i < n) out[i] = make_float2(L[j].x, L[j].y);
+    }
 }
 
 // ------------------------------------------------------------------ 3D walk
@@ -472,12 +512,14 @@ orand_status_t orand_brownian_walk(const orand_walk2d_t *p, float *pos_out, cuda
     if (p->n_particles == 0) return ORAND_OK;
     orand_status_t st = check_ptr(pos_out, 8);
     if (st != ORAND_OK) return st;
-    if (!walk_grid_ok(p->n_particles)) return ORAND_ERR_OVERFLOW;
+    if (p->steps == UINT32_MAX) return ORAND_ERR_OVERFLOW;  // counters 1..steps, same limit as the 3D walk
+    const uint64_t grid = ceil_div(p->n_particles, (uint64_t)kWalk2dBlock * kWalk2dPerThread);
+    if (grid > 0x7FFFFFFFull) return ORAND_ERR_OVERFLOW;
     DeviceInfo info;
     if ((st = current_device(&info)) != ORAND_OK) return st;
     const float s = (float)sqrt(2.0 * (double)p->D * (double)p->dt);
-    walk2d_kernel<<<walk_grid(p->n_particles), kWalkBlock, 0, stream>>>(p->n_particles, p->p_first, p->seed,
-                                                                      p->steps, s, (float2 *)pos_out);
+    walk2d_kernel<<<(unsigned)grid, kWalk2dBlock, 0, stream>>>(p->n_particles, p->p_first, p->seed, p->steps, s,
+                                                              (float2 *)pos_out);
     return launch_status();
 }
 

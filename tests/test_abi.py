@@ -80,6 +80,7 @@ def test_walk_arguments_rejected_on_host(lib):
     assert lib.orand_brownian_walk(ctypes.byref(W2(4, 10)), None, None) == -1           # NULL output
     assert lib.orand_brownian_walk(ctypes.byref(W2(4, 10)), 4, None) == -3              # not 8-byte aligned
     assert lib.orand_brownian_walk(ctypes.byref(W2(8, 10, p_first=2**64 - 4)), 8, None) == -2
+    assert lib.orand_brownian_walk(ctypes.byref(W2(8, 2**32 - 1)), 8, None) == -2        # counter 2^32 - 1 limit
     p3 = orand.walk3d_params(10, 5)
     assert lib.orand_walk3d_fwd(None, ctypes.byref(p3), None, 16, None, None, None) == -1  # no context
     assert lib.orand_walk3d_fwd(None, None, None, 16, None, None, None) == -1
