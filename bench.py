@@ -234,6 +234,31 @@ def ragged_rows(torch, orand, W, rank):
     return [row], {"ragged_out": out, "recs": recs}
 
 
+def stream_test_rows(torch, orand, W, rank, n_words=1 << 30):
+    """The parallel-stream battery (§5, Statistical Evaluation) per generator:
+    16,000 particles x 3-word micro-streams, lengthened to about 2^30 words,
+    generated and counted on the GPU.  Rank r tests the iterations after
+    those of ranks 0..r-1."""
+    from paper_2310_19925_b300 import stream_tests as ST
+
+    rows, keep = [], []
+    for gen in (W.PHILOX, W.THREEFRY, W.SQUARES, W.TYCHE):
+        b = ST.Battery(gen, seed=0, n_words=n_words)
+        b.counter_first = rank * b.n_iter
+        keep.append(b)
+        row = Row("stream_tests/%s" % W.GEN_NAMES[gen], lambda sh, b=b: b.launch(sh), b.words, "words",
+                  b.kernels_per_launch)
+
+        def finish(b=b):
+            res = b.results()
+            return {"p_values": {k: round(v["p"], 6) for k, v in res.items()},
+                    "verdicts": sorted({v["verdict"] for v in res.values()})}
+
+        row.finish = finish
+        rows.append(row)
+    return rows, keep
+
+
 def ragged_serial_baseline(torch, orand, W, n_sub=2000, reps=2):
     """One bulk-fill launch per request (in order, one stream) vs the batcher,
     on the first n_sub requests of the list (the full list's serial Tyche
@@ -472,10 +497,11 @@ def main():
     head = frows[0]  # fill/philox4x32_10/u32: the headline kernel
     wrows, _wkeep = walk_rows(torch, orand, W, rank)
     rrows, _rkeep = ragged_rows(torch, orand, W, rank)
-    # Step order: walks, ragged batch, then the fills with the headline
-    # Philox u32 fill last, right after the Philox f32 fill, so that it runs
-    # behind a kernel of its own kind rather than behind the 30 GB batch.
-    rows = wrows + rrows + frows[::-1]
+    srows, _skeep = stream_test_rows(torch, orand, W, rank)
+    # Step order: walks, ragged batch, stream tests, then the fills with the
+    # headline Philox u32 fill last, right after the Philox f32 fill, so that
+    # it runs behind a kernel of its own kind rather than behind the 30 GB batch.
+    rows = wrows + rrows + srows + frows[::-1]
     if args.only:
         rows = [r for r in rows if args.only in r.name]
         if head not in rows:
@@ -538,6 +564,8 @@ def main():
             e["GB/s"] = round(world * r.bytes_written / (t * 1e-3) / 1e9, 1)
             e["frac_hbm"] = round(r.bytes_written / (t * 1e-3) / 1e9 / peak, 4)
         e.update(getattr(r, "extra", {}))
+        if hasattr(r, "finish"):
+            e.update(r.finish())
         row_table[r.name] = e
 
     # End to end through the C ABI: the same fill, then the 1 GiB result read

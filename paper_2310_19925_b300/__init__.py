@@ -73,6 +73,10 @@ _SIGS = {
     "orand_langevin2d_curand_setup": (_i32, [_vp, _vp, _vp, _u64, _vp]),
     "orand_langevin2d_curand_step": (_i32, [_vp, _vp, _vp, _vp]),
     "orand_fill_ragged": (_i32, [_vp, _vp, _sz, _vp, _u64, _vp]),
+    "orand_fill_micro_streams": (_i32, [_i32, _u64, _u64, _u32, _u32, _u32, _vp, _vp]),
+    "orand_stat_tuples": (_i32, [_vp, _u64, _u32, _u32, _u32, _u32, _vp, _vp]),
+    "orand_stat_gaps": (_i32, [_vp, _vp, _u64, _u64, _u64, _u32, _vp, _vp, _vp]),
+    "orand_stat_birthday": (_i32, [_vp, _u64, _u32, _u32, _u32, _u32, _vp, _vp]),
     "orand_fill_ragged_serial": (_i32, [_vp, _sz, _vp, _u64, _vp]),
     "orand_ragged_set_config": (_i32, [_vp, _vp]),
     "orand_ragged_get_config": (_i32, [_vp, _vp]),
@@ -240,6 +244,94 @@ def fill(gen: int, dtype: int, seed: int, counter: int, n_streams: int, draws_pe
     orand_fill(gen, dtype, seed, counter, n_streams, draws_per_stream, _ptr(out) if n else 0,
                _stream_handle(stream))
     return out
+
+
+# ------------------------------------------- parallel-stream statistics --
+
+GAP_NO_HIT = 2**64 - 1
+
+
+def orand_fill_micro_streams(gen, seed, n_streams, draws, counter_first, n_counters, out_ptr, stream_handle):
+    _check(_lib().orand_fill_micro_streams(gen, seed & (2**64 - 1), n_streams, draws, counter_first & 0xFFFFFFFF,
+                                           n_counters, out_ptr, stream_handle), "orand_fill_micro_streams")
+
+
+def orand_stat_tuples(words_ptr, n_words, t, bits, shift, stride, counts_ptr, stream_handle):
+    _check(_lib().orand_stat_tuples(words_ptr, n_words, t, bits, shift, stride, counts_ptr, stream_handle),
+           "orand_stat_tuples")
+
+
+def orand_stat_gaps(ctx, words_ptr, n_words, lo, hi, t_max, counts_ptr, carry_ptr, stream_handle):
+    _check(_lib().orand_stat_gaps(ctx, words_ptr, n_words, lo, hi, t_max, counts_ptr, carry_ptr, stream_handle),
+           "orand_stat_gaps")
+
+
+def orand_stat_birthday(words_ptr, n_words, log2_n, bits, shift, r_max, counts_ptr, stream_handle):
+    _check(_lib().orand_stat_birthday(words_ptr, n_words, log2_n, bits, shift, r_max, counts_ptr, stream_handle),
+           "orand_stat_birthday")
+
+
+def fill_micro_streams(gen, seed, n_streams, draws, counter_first, n_counters, out=None, stream=None):
+    """The concatenated micro-stream as a CUDA int32 tensor (u32 bits) of
+    n_counters * n_streams * draws words."""
+    import torch
+
+    n = n_counters * n_streams * draws
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+    if out.numel() < n or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA tensor with at least %d elements" % n)
+    orand_fill_micro_streams(gen, seed, n_streams, draws, counter_first, n_counters, _ptr(out) if n else 0,
+                             _stream_handle(stream))
+    return out
+
+
+def _counts(n, counts):
+    import torch
+
+    if counts is None:
+        counts = torch.zeros(n, dtype=torch.int64, device="cuda")
+    if counts.numel() != n or counts.dtype != torch.int64 or not counts.is_cuda:
+        raise ValueError("counts must be a CUDA int64 tensor of %d elements" % n)
+    return counts
+
+
+def _words(words):
+    if not words.is_cuda or not words.is_contiguous() or words.element_size() != 4:
+        raise ValueError("words must be a contiguous CUDA tensor of 32-bit elements")
+    return words
+
+
+def stat_tuples(words, t, bits, shift, stride, counts=None, stream=None):
+    """Accumulate tuple counts (2^(t*bits) int64) of a CUDA u32/int32 tensor."""
+    w = _words(words)
+    c = _counts(1 << (t * bits), counts)
+    orand_stat_tuples(_ptr(w) if w.numel() else 0, w.numel(), t, bits, shift, stride, _ptr(c), _stream_handle(stream))
+    return c
+
+
+def stat_gaps(words, lo, hi, t_max, counts=None, carry=None, stream=None):
+    """Accumulate gap counts (t_max + 1 int64); `carry` is a 1-element CUDA
+    int64 tensor holding the open run (GAP_NO_HIT bits before the first hit).
+    Returns (counts, carry)."""
+    import torch
+
+    w = _words(words)
+    c = _counts(t_max + 1, counts)
+    if carry is None:
+        carry = torch.full((1,), -1, dtype=torch.int64, device="cuda")   # all ones = GAP_NO_HIT
+    orand_stat_gaps(default_context().handle, _ptr(w) if w.numel() else 0, w.numel(), lo, hi, t_max, _ptr(c),
+                    _ptr(carry), _stream_handle(stream))
+    return c, carry
+
+
+def stat_birthday(words, log2_n, bits, shift, r_max, counts=None, stream=None):
+    """Accumulate birthday-spacing counts (r_max + 1 int64) over whole samples of 2^log2_n words."""
+    w = _words(words)
+    c = _counts(r_max + 1, counts)
+    orand_stat_birthday(_ptr(w) if w.numel() else 0, w.numel(), log2_n, bits, shift, r_max, _ptr(c),
+                        _stream_handle(stream))
+    return c
 
 
 # ------------------------------------------------------------------ walks --

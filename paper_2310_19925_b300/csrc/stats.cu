@@ -1,0 +1,378 @@
+// The parallel-stream correlation harness (§5, Statistical Evaluation) on
+// the GPU: the concatenated micro-stream generator and three counting
+// kernels (tuple frequencies, gap test, birthday spacings; Knuth, TAOCP
+// vol. 2, §3.3.2).  All outputs are integer counts accumulated with atomics,
+// so every launch shape gives the same counts.
+//
+//   micro_stream_kernel  one thread per (iteration, particle) micro-stream;
+//                        a warp writes 32 * draws consecutive words.
+//   tuple_kernel         grid-stride over tuples; per-CTA shared-memory
+//                        histogram, flushed once per CTA.
+//   gap_span_kernel      one warp per span of 8192 words, read 32 words at a
+//                        time (coalesced); a ballot of the hits gives each
+//                        hit's distance to the previous one by bit scans.
+//                        The span's first and last hit go to scratch.
+//   gap_stitch_kernel    the gap before each span's first hit, from the
+//                        previous non-empty span or the carried run.
+//   gap_carry_kernel     the run of non-hits after the piece's last hit.
+//   birthday_kernel      one CTA per sample: bitonic sorts of the birthdays
+//                        and of the spacings in shared memory.
+#include "common.cuh"
+#include "ctx.cuh"
+#include "orand_device.cuh"
+#include "orand_stats.h"
+#include "values.cuh"
+
+namespace orand_impl {
+
+// ------------------------------------------------------- micro-streams
+
+struct MicroArgs {
+    uint64_t seed, n_streams, n_micro;  // n_micro = n_counters * n_streams
+    uint64_t stride_div, stride_mod;    // grid stride split into (iterations, particles)
+    uint32_t draws, counter_first;
+    uint32_t *out;
+};
+
+template <int GEN>
+__global__ void __launch_bounds__(256) micro_stream_kernel(MicroArgs a)
+{
+    uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.n_micro) return;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t j = m / a.n_streams, s = m - j * a.n_streams;
+    for (;;) {
+        uint32_t *o = a.out + m * a.draws;
+        const uint64_t key = a.seed ^ s;
+        const uint32_t ctr = a.counter_first + (uint32_t)j;
+        if (GEN == ORAND_TYCHE) {
+            orand::TycheState st = orand::tyche_init(key, ctr);
+            for (uint32_t k = 0; k < a.draws; ++k) o[k] = orand::tyche_next(st);
+        } else {
+            for (uint32_t b = 0; 4 * b < a.draws; ++b) {
+                const uint4 w = group_words<GEN>(key, ctr, b);
+                const uint32_t k = 4 * b, left = a.draws - k;
+                o[k] = w.x;
+                if (left > 1) o[k + 1] = w.y;
+                if (left > 2) o[k + 2] = w.z;
+                if (left > 3) o[k + 3] = w.w;
+            }
+        }
+        m += stride;
+        if (m >= a.n_micro) break;
+        j += a.stride_div;
+        s += a.stride_mod;
+        if (s >= a.n_streams) {
+            s -= a.n_streams;
+            ++j;
+        }
+    }
+}
+
+// --------------------------------------------------------------- tuples
+
+__global__ void __launch_bounds__(256) tuple_kernel(const uint32_t *__restrict__ w, uint64_t n_tuples, uint32_t t,
+                                                    uint32_t bits, uint32_t shift, uint32_t stride, uint32_t cells,
+                                                    unsigned long long *__restrict__ counts)
+{
+    extern __shared__ uint32_t hist[];
+    for (uint32_t i = threadIdx.x; i < cells; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const uint32_t mask = (1u << bits) - 1u;  // bits <= 14
+    const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n_tuples; m += gstride) {
+        const uint32_t *p = w + m * stride;
+        uint32_t cell = 0u;
+        for (uint32_t i = 0; i < t; ++i) cell = (cell << bits) | ((__ldg(p + i) >> shift) & mask);
+        atomicAdd(&hist[cell], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cells; i += blockDim.x)
+        if (hist[i]) atomicAdd(&counts[i], (unsigned long long)hist[i]);
+}
+
+// ----------------------------------------------------------------- gaps
+
+constexpr uint32_t kGapSpan = 8192;  // words per warp span (256 steps of 32)
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool gap_hit(uint32_t x, uint64_t lo, uint64_t hi)
+{
+    return (uint64_t)x >= lo && (uint64_t)x < hi;
+}
+
+// Per span: gaps between hits inside the span into the histogram, and the
+// span-local offsets of its first and last hit (kNone when it has none).
+__global__ void __launch_bounds__(256) gap_span_kernel(const uint32_t *__restrict__ w, uint64_t n, uint64_t lo,
+                                                       uint64_t hi, uint32_t t_max,
+                                                       unsigned long long *__restrict__ counts,
+                                                       uint32_t *__restrict__ span_first,
+                                                       uint32_t *__restrict__ span_last, uint64_t n_spans)
+{
+    extern __shared__ uint32_t hist[];
+    for (uint32_t i = threadIdx.x; i <= t_max; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t sp = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); sp < n_spans; sp += warps) {
+        const uint64_t start = sp * kGapSpan;
+        uint32_t first = kNone, last = kNone;  // span-local offsets, warp-uniform
+        for (uint32_t it = 0; it < kGapSpan / 32; ++it) {
+            const uint64_t base = start + (uint64_t)it * 32;
+            if (base >= n) break;
+            const uint64_t idx = base + lane;
+            const bool hit = idx < n && gap_hit(__ldg(w + idx), lo, hi);
+            const uint32_t mask = __ballot_sync(0xFFFFFFFFu, hit);
+            if (hit) {
+                const uint32_t below = mask & ((1u << lane) - 1u);
+                uint32_t gap = kNone;
+                if (below) gap = lane - (31u - __clz(below)) - 1u;
+                else if (last != kNone) gap = it * 32 + lane - last - 1u;
+                if (gap != kNone) atomicAdd(&hist[min(gap, t_max)], 1u);
+            }
+            if (mask) {
+                if (first == kNone) first = it * 32 + (__ffs(mask) - 1);
+                last = it * 32 + (31u - __clz(mask));
+            }
+        }
+        if (lane == 0) {
+            span_first[sp] = first;
+            span_last[sp] = last;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i <= t_max; i += blockDim.x)
+        if (hist[i]) atomicAdd(&counts[i], (unsigned long long)hist[i]);
+}
+
+// The gap that ends at each non-empty span's first hit.
+__global__ void __launch_bounds__(256) gap_stitch_kernel(const uint32_t *__restrict__ span_first,
+                                                         const uint32_t *__restrict__ span_last, uint64_t n_spans,
+                                                         const unsigned long long *__restrict__ carry, uint32_t t_max,
+                                                         unsigned long long *__restrict__ counts)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_spans || span_first[i] == kNone) return;
+    const uint64_t pos = i * kGapSpan + span_first[i];
+    uint64_t gap = ORAND_GAP_NO_HIT;
+    uint64_t k = i;
+    while (k > 0) {  // nearest earlier span with a hit
+        --k;
+        if (span_last[k] != kNone) {
+            gap = pos - (k * kGapSpan + span_last[k]) - 1;
+            break;
+        }
+    }
+    if (gap == ORAND_GAP_NO_HIT && *carry != ORAND_GAP_NO_HIT) gap = *carry + pos;
+    if (gap != ORAND_GAP_NO_HIT) atomicAdd(&counts[gap < t_max ? gap : t_max], 1ull);
+}
+
+// The carry after this piece: non-hits after its last hit, or the old
+// carry grown by n when the piece has no hit.  One warp.
+__global__ void gap_carry_kernel(const uint32_t *__restrict__ span_last, uint64_t n_spans, uint64_t n,
+                                 unsigned long long *__restrict__ carry)
+{
+    const uint32_t lane = threadIdx.x;
+    for (uint64_t end = n_spans; end > 0; end = end > 32 ? end - 32 : 0) {
+        const bool ok = lane < end && span_last[end - 1 - lane] != kNone;
+        const uint32_t mask = __ballot_sync(0xFFFFFFFFu, ok);
+        if (mask) {
+            const uint64_t k = end - 1 - (uint64_t)(__ffs(mask) - 1);  // the last non-empty span
+            if (lane == 0) *carry = n - 1 - (k * kGapSpan + span_last[k]);
+            return;
+        }
+    }
+    if (lane == 0 && *carry != ORAND_GAP_NO_HIT) *carry += n;
+}
+
+// ------------------------------------------------------------- birthday
+
+constexpr int kBirthdayBlock = 512;
+
+// Ascending bitonic sort of y[0..n) (n a power of two) by the whole block.
+__device__ __forceinline__ void block_bitonic_sort(unsigned long long *y, uint32_t n)
+{
+    for (uint32_t k = 2; k <= n; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t p = threadIdx.x; p < n / 2; p += blockDim.x) {
+                const uint32_t lo = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+                const uint32_t hi = lo + j;
+                const unsigned long long a = y[lo], b = y[hi];
+                if ((a > b) == ((lo & k) == 0)) {
+                    y[lo] = b;
+                    y[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBirthdayBlock) birthday_kernel(const uint32_t *__restrict__ w, uint64_t n_samples,
+                                                                  uint32_t log2_n, uint32_t bits, uint32_t shift,
+                                                                  uint32_t r_max,
+                                                                  unsigned long long *__restrict__ counts)
+{
+    extern __shared__ unsigned long long y[];
+    __shared__ uint32_t red[kBirthdayBlock / 32];
+    const uint32_t n = 1u << log2_n;
+    const unsigned long long m = 1ull << bits;
+    const unsigned long long mask = m - 1ull;
+    constexpr uint32_t kMaxPer = 4096 / kBirthdayBlock;
+    for (uint64_t q = blockIdx.x; q < n_samples; q += gridDim.x) {
+        const uint32_t *p = w + q * n;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) y[i] = ((unsigned long long)__ldg(p + i) >> shift) & mask;
+        __syncthreads();
+        block_bitonic_sort(y, n);
+        unsigned long long sp[kMaxPer];
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxPer; ++k) {
+            const uint32_t i = threadIdx.x + k * blockDim.x;
+            if (i < n) sp[k] = (i + 1 < n) ? y[i + 1] - y[i] : y[0] + m - y[n - 1];
+        }
+        __syncthreads();
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxPer; ++k) {
+            const uint32_t i = threadIdx.x + k * blockDim.x;
+            if (i < n) y[i] = sp[k];
+        }
+        __syncthreads();
+        block_bitonic_sort(y, n);
+        uint32_t r = 0;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) r += (i > 0 && y[i] == y[i - 1]) ? 1u : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xFFFFFFFFu, r, o);
+        if ((threadIdx.x & 31u) == 0) red[threadIdx.x >> 5] = r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t R = 0;
+            for (uint32_t i = 0; i < blockDim.x / 32; ++i) R += red[i];
+            atomicAdd(&counts[R < r_max ? R : r_max], 1ull);
+        }
+        __syncthreads();
+    }
+}
+
+static orand_status_t check_buf(const void *ptr, size_t align)
+{
+    if (ptr == nullptr) return ORAND_ERR_INVALID_ARG;
+    return ((uintptr_t)ptr % align) ? ORAND_ERR_ALIGNMENT : ORAND_OK;
+}
+
+}  // namespace orand_impl
+
+using namespace orand_impl;
+
+extern "C" {
+
+orand_status_t orand_fill_micro_streams(orand_gen_t gen, uint64_t seed, uint64_t n_streams, uint32_t draws,
+                                        uint32_t counter_first, uint32_t n_counters, uint32_t *out,
+                                        cudaStream_t stream)
+{
+    if ((unsigned)gen > ORAND_TYCHE || draws == 0 || draws > 64) return ORAND_ERR_INVALID_ARG;
+    if (n_counters > 0 && (uint64_t)counter_first + n_counters - 1 > UINT32_MAX) return ORAND_ERR_OVERFLOW;
+    uint64_t n_micro, n_words;
+    if (mul_overflows(n_streams, n_counters, &n_micro) || mul_overflows(n_micro, draws, &n_words) ||
+        n_words > (1ull << 62))
+        return ORAND_ERR_OVERFLOW;
+    if (n_words == 0) return ORAND_OK;
+    orand_status_t st = check_buf(out, 4);
+    if (st != ORAND_OK) return st;
+    DeviceInfo info;
+    if ((st = current_device(&info)) != ORAND_OK) return st;
+    MicroArgs a;
+    a.seed = seed;
+    a.n_streams = n_streams;
+    a.n_micro = n_micro;
+    a.draws = draws;
+    a.counter_first = counter_first;
+    a.out = out;
+    const unsigned grid = grid_for(n_micro, 256, info.sm_count, 8);
+    const uint64_t stride = (uint64_t)grid * 256;
+    a.stride_div = stride / n_streams;
+    a.stride_mod = stride % n_streams;
+    switch (gen) {
+    case ORAND_PHILOX4x32_10: micro_stream_kernel<ORAND_PHILOX4x32_10><<<grid, 256, 0, stream>>>(a); break;
+    case ORAND_THREEFRY4x32_20: micro_stream_kernel<ORAND_THREEFRY4x32_20><<<grid, 256, 0, stream>>>(a); break;
+    case ORAND_SQUARES32: micro_stream_kernel<ORAND_SQUARES32><<<grid, 256, 0, stream>>>(a); break;
+    default: micro_stream_kernel<ORAND_TYCHE><<<grid, 256, 0, stream>>>(a); break;
+    }
+    return launch_status();
+}
+
+orand_status_t orand_stat_tuples(const uint32_t *words, uint64_t n_words, uint32_t t, uint32_t bits,
+                                 uint32_t shift, uint32_t stride, uint64_t *counts, cudaStream_t stream)
+{
+    if (t < 1 || t > 4 || bits < 1 || t * bits > 14 || shift + bits > 32 || stride < 1) return ORAND_ERR_INVALID_ARG;
+    orand_status_t st = check_buf(counts, 8);
+    if (st != ORAND_OK) return st;
+    const uint64_t n_tuples = n_words < t ? 0 : (n_words - t) / stride + 1;
+    if (n_tuples == 0) return ORAND_OK;
+    if ((st = check_buf(words, 4)) != ORAND_OK) return st;
+    DeviceInfo info;
+    if ((st = current_device(&info)) != ORAND_OK) return st;
+    const uint32_t cells = 1u << (t * bits);
+    const size_t smem = (size_t)cells * sizeof(uint32_t);
+    if (smem > 48 * 1024)
+        ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // Per-CTA u32 counters: launch pieces small enough that no CTA passes 2^31.
+    const uint64_t piece = 1ull << 36;
+    for (uint64_t m0 = 0; m0 < n_tuples; m0 += piece) {
+        const uint64_t nt = n_tuples - m0 < piece ? n_tuples - m0 : piece;
+        const unsigned grid = grid_for(nt, 256, info.sm_count, 4);
+        tuple_kernel<<<grid, 256, smem, stream>>>(words + m0 * stride, nt, t, bits, shift, stride, cells,
+                                                  (unsigned long long *)counts);
+        if ((st = launch_status()) != ORAND_OK) return st;
+    }
+    return ORAND_OK;
+}
+
+orand_status_t orand_stat_gaps(orand_ctx_t ctx, const uint32_t *words, uint64_t n_words, uint64_t lo, uint64_t hi,
+                               uint32_t t_max, uint64_t *counts, uint64_t *carry, cudaStream_t stream)
+{
+    if (lo >= hi || hi > (1ull << 32) || t_max < 1 || t_max > 4096) return ORAND_ERR_INVALID_ARG;
+    orand_status_t st;
+    if ((st = check_buf(counts, 8)) != ORAND_OK || (st = check_buf(carry, 8)) != ORAND_OK) return st;
+    if (n_words == 0) return ORAND_OK;
+    if ((st = check_buf(words, 4)) != ORAND_OK) return st;
+    if (n_words > (1ull << 50)) return ORAND_ERR_OVERFLOW;
+    const uint64_t n_spans = ceil_div(n_words, kGapSpan);
+    void *scr;
+    if ((st = ctx_scratch(ctx, n_spans * 2 * sizeof(uint32_t), &scr)) != ORAND_OK) return st;
+    uint32_t *span_first = (uint32_t *)scr, *span_last = span_first + n_spans;
+    DeviceInfo info;
+    if ((st = current_device(&info)) != ORAND_OK) return st;
+    const size_t smem = (size_t)(t_max + 1) * sizeof(uint32_t);
+    const unsigned grid = grid_for(n_spans * 32, 256, info.sm_count, 8);
+    gap_span_kernel<<<grid, 256, smem, stream>>>(words, n_words, lo, hi, t_max, (unsigned long long *)counts,
+                                                 span_first, span_last, n_spans);
+    if ((st = launch_status()) != ORAND_OK) return st;
+    gap_stitch_kernel<<<(unsigned)ceil_div(n_spans, 256), 256, 0, stream>>>(
+        span_first, span_last, n_spans, (const unsigned long long *)carry, t_max, (unsigned long long *)counts);
+    if ((st = launch_status()) != ORAND_OK) return st;
+    gap_carry_kernel<<<1, 32, 0, stream>>>(span_last, n_spans, n_words, (unsigned long long *)carry);
+    return launch_status();
+}
+
+orand_status_t orand_stat_birthday(const uint32_t *words, uint64_t n_words, uint32_t log2_n, uint32_t bits,
+                                   uint32_t shift, uint32_t r_max, uint64_t *counts, cudaStream_t stream)
+{
+    if (log2_n < 2 || log2_n > 12 || bits < 1 || bits > 32 || shift + bits > 32 || r_max < 1 || r_max > 4096)
+        return ORAND_ERR_INVALID_ARG;
+    orand_status_t st = check_buf(counts, 8);
+    if (st != ORAND_OK) return st;
+    const uint64_t n_samples = n_words >> log2_n;
+    if (n_samples == 0) return ORAND_OK;
+    if ((st = check_buf(words, 4)) != ORAND_OK) return st;
+    DeviceInfo info;
+    if ((st = current_device(&info)) != ORAND_OK) return st;
+    const uint32_t n = 1u << log2_n;
+    const unsigned block = n / 2 < (uint32_t)kBirthdayBlock ? (n / 2 < 32 ? 32 : n / 2) : kBirthdayBlock;
+    const size_t smem = (size_t)n * sizeof(unsigned long long);
+    const unsigned grid = (unsigned)(n_samples < (uint64_t)info.sm_count * 4 ? n_samples : (uint64_t)info.sm_count * 4);
+    birthday_kernel<<<grid, block, smem, stream>>>(words, n_samples, log2_n, bits, shift, r_max,
+                                                   (unsigned long long *)counts);
+    return launch_status();
+}
+
+}  // extern "C"

@@ -10,12 +10,15 @@ import pytest
 import paper_2310_19925_b300 as orand
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
 
 
 def _declared_functions():
     names = set()
-    for h in ("orand.h",):
-        src = open(os.path.join(ROOT, "include", h)).read()
+    for h in sorted(os.listdir(INCLUDE)):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(INCLUDE, h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names |= set(re.findall(r"\b(orand_[a-z0-9_]+)\s*\(", src))
     return sorted(names)
@@ -31,7 +34,7 @@ def lib():
 
 def test_exports_every_declared_symbol(lib):
     declared = _declared_functions()
-    assert "orand_fill_u32" in declared and len(declared) >= 8
+    assert "orand_fill_u32" in declared and "orand_stat_gaps" in declared and len(declared) >= 8
     for name in declared:
         assert hasattr(lib, name), name
         assert name in orand._SIGS, "binding lacks " + name
@@ -147,3 +150,31 @@ def test_langevin_arguments_rejected_on_host(lib):
     assert lib.orand_langevin2d_fused(ctypes.byref(P(4)), 16, 2**32 - 5, 10, None) == -2  # counters wrap
     assert lib.orand_langevin2d_curand_setup(ctypes.byref(P(4)), 16, None, 1984, None) == -1
     assert lib.orand_langevin2d_curand_state_bytes() >= 48
+
+
+def test_stream_statistics_arguments_rejected_on_host(lib):
+    L = lib
+    assert L.orand_fill_micro_streams(9, 0, 10, 3, 0, 1, 16, None) == -1          # unknown generator
+    assert L.orand_fill_micro_streams(0, 0, 10, 0, 0, 1, 16, None) == -1          # draws = 0
+    assert L.orand_fill_micro_streams(0, 0, 10, 65, 0, 1, 16, None) == -1         # draws > 64
+    assert L.orand_fill_micro_streams(0, 0, 10, 3, 2**32 - 2, 3, 16, None) == -2  # counters wrap
+    assert L.orand_fill_micro_streams(0, 0, 2**62, 3, 0, 2, 16, None) == -2       # size overflow
+    assert L.orand_fill_micro_streams(0, 0, 10, 3, 0, 0, None, None) == 0         # empty: no-op
+    assert L.orand_fill_micro_streams(0, 0, 10, 3, 0, 1, None, None) == -1        # NULL output
+    assert L.orand_fill_micro_streams(0, 0, 10, 3, 0, 1, 2, None) == -3           # misaligned output
+    assert L.orand_stat_tuples(16, 100, 0, 8, 24, 1, 16, None) == -1              # t = 0
+    assert L.orand_stat_tuples(16, 100, 3, 5, 0, 3, 16, None) == -1               # 15 bits of cells
+    assert L.orand_stat_tuples(16, 100, 1, 8, 25, 1, 16, None) == -1              # field past bit 31
+    assert L.orand_stat_tuples(16, 100, 1, 8, 24, 0, 16, None) == -1              # stride 0
+    assert L.orand_stat_tuples(16, 100, 1, 8, 24, 1, 4, None) == -3               # counts misaligned
+    assert L.orand_stat_tuples(None, 0, 1, 8, 24, 1, 16, None) == 0               # no tuple: no-op
+    assert L.orand_stat_gaps(None, 16, 10, 5, 5, 8, 16, 16, None) == -1           # lo >= hi
+    assert L.orand_stat_gaps(None, 16, 10, 0, 2**32 + 1, 8, 16, 16, None) == -1   # hi > 2^32
+    assert L.orand_stat_gaps(None, 16, 10, 0, 16, 0, 16, 16, None) == -1          # t_max = 0
+    assert L.orand_stat_gaps(None, 16, 10, 0, 16, 8, 16, None, None) == -1        # NULL carry
+    assert L.orand_stat_gaps(None, 16, 10, 0, 16, 8, 16, 16, None) == -1          # NULL context
+    assert L.orand_stat_birthday(16, 100, 1, 32, 0, 8, 16, None) == -1            # log2_n < 2
+    assert L.orand_stat_birthday(16, 100, 13, 32, 0, 8, 16, None) == -1           # log2_n > 12
+    assert L.orand_stat_birthday(16, 100, 4, 24, 9, 8, 16, None) == -1            # field past bit 31
+    assert L.orand_stat_birthday(16, 100, 4, 24, 8, 0, 16, None) == -1            # r_max = 0
+    assert L.orand_stat_birthday(16, 15, 4, 24, 8, 8, 16, None) == 0              # no whole sample

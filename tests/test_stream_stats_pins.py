@@ -194,3 +194,55 @@ def test_planted_low_bit_alternation_fails():
     c = S.tuple_counts(w, 2, 1, 0, 1)
     assert c[0] == 0 and c[3] == 0
     assert stats.chisquare(c.astype(float)).pvalue < 1e-30
+
+
+# ------------------------------------------- host-side evaluation (product) ----
+
+def test_evaluate_matches_scipy_and_flags_failures():
+    """The harness's p-values (paper_2310_19925_b300.stream_tests.evaluate)
+    against scipy's tests on the same counts, and its verdicts on good and
+    planted-bad counts from the oracle."""
+    from paper_2310_19925_b300 import stream_tests as ST
+
+    w = pcg_words(48000 * 40)
+    for name, kind, prm in ST.BATTERY:
+        if kind == "tuples":
+            c = S.tuple_counts(w, prm["t"], prm["bits"], prm["shift"], prm["stride"])
+        elif kind == "gaps":
+            c, _ = S.gap_counts(w, prm["lo"], prm["hi"], prm["t_max"])
+        else:
+            c = S.birthday_counts(w, prm["log2_n"], prm["bits"], prm["shift"], prm["r_max"])
+        r = ST.evaluate(kind, prm, c)
+        assert r["verdict"] == "pass", (name, r["p"])
+        if kind == "birthday":
+            y = int(np.dot(np.arange(c.size), c.astype(np.int64)))
+            mu = c.sum() * ST.birthday_mean(prm["log2_n"], prm["bits"])
+            assert r["p"] == pytest.approx(min(1, 2 * min(stats.poisson.cdf(y, mu), stats.poisson.sf(y - 1, mu))))
+            continue
+        probs = ST.expected_probabilities(kind, prm)
+        assert abs(probs.sum() - 1.0) < 1e-12
+        exp = probs * c.sum()
+        if exp.min() >= 5:
+            assert r["p"] == pytest.approx(stats.chisquare(c.astype(float), exp).pvalue, rel=1e-9)
+    bad = np.zeros(256, np.uint64)
+    bad[:128] = 1000
+    assert ST.evaluate("tuples", dict(t=1, bits=8, shift=24, stride=1), bad)["verdict"] == "fail"
+
+
+def test_birthday_mean_against_brute_force():
+    """E[R] = n (n-1)^2 / (4m) - n (n-1)^2 (n-2)^2 / (18 m^2), the mean the
+    harness tests against, pinned by the oracle's own counts where the two
+    corrections to Knuth's n^3 / (4m) are large: n = 64, m = 2^16 (lambda = 1;
+    pairs 0.96899 minus triples 0.01263 gives 0.95636), 400,000 samples
+    (standard error 0.0015)."""
+    from paper_2310_19925_b300 import stream_tests as ST
+
+    rng = np.random.default_rng(2024)
+    n_samples = 400_000
+    c = S.birthday_counts(pcg_words(64 * n_samples, rng), 6, 16, 0, 200)
+    mean = float(np.dot(np.arange(201), c)) / n_samples
+    se = math.sqrt(1.0 / n_samples)
+    want = ST.birthday_mean(6, 16)
+    assert abs(want - 0.95636) < 1e-5
+    assert abs(mean - want) < 4 * se
+    assert abs(mean - 1.0) > 10 * se          # Knuth's first-order mean is off by > 10 standard errors
