@@ -7,7 +7,8 @@
 //   micro_stream_kernel  one thread per (iteration, particle) micro-stream;
 //                        a warp writes 32 * draws consecutive words.
 //   tuple_kernel         grid-stride over tuples; per-CTA shared-memory
-//                        histogram, flushed once per CTA.
+//                        histogram (a column per lane for up to 256 cells),
+//                        flushed once per CTA.
 //   gap_span_kernel      one warp per span of 8192 words, read 32 words at a
 //                        time (coalesced); a ballot of the hits gives each
 //                        hit's distance to the previous one by bit scans.
@@ -15,8 +16,9 @@
 //   gap_stitch_kernel    the gap before each span's first hit, from the
 //                        previous non-empty span or the carried run.
 //   gap_carry_kernel     the run of non-hits after the piece's last hit.
-//   birthday_kernel      one CTA per sample: bitonic sorts of the birthdays
-//                        and of the spacings in shared memory.
+//   birthday_kernel      one CTA per sample: counting sort of the birthdays
+//                        in shared memory, distinct spacings counted in a
+//                        shared-memory hash set.
 #include "common.cuh"
 #include "ctx.cuh"
 #include "orand_device.cuh"
@@ -71,29 +73,53 @@ __global__ void __launch_bounds__(256) micro_stream_kernel(MicroArgs a)
 
 // --------------------------------------------------------------- tuples
 
+// LANES = 32: cells of at most 256, each lane counting in its own column
+// (hist[cell * 32 + lane]), so a warp's atomics never share a bank or an
+// address.  LANES = 1: one column, for up to 2^14 cells.
+constexpr int kTupleUnroll = 8;  // tuples per thread per pass, all loads issued before the atomics
+
+// LANES = 32: cells of at most 256, each lane counting in its own column
+// (hist[cell * 32 + lane]), so a warp's atomics never share a bank or an
+// address.  LANES = 1: one column, for up to 2^14 cells.
+template <int LANES>
 __global__ void __launch_bounds__(256) tuple_kernel(const uint32_t *__restrict__ w, uint64_t n_tuples, uint32_t t,
                                                     uint32_t bits, uint32_t shift, uint32_t stride, uint32_t cells,
                                                     unsigned long long *__restrict__ counts)
 {
     extern __shared__ uint32_t hist[];
-    for (uint32_t i = threadIdx.x; i < cells; i += blockDim.x) hist[i] = 0u;
+    for (uint32_t i = threadIdx.x; i < cells * LANES; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     const uint32_t mask = (1u << bits) - 1u;  // bits <= 14
+    const uint32_t col = LANES == 1 ? 0u : (threadIdx.x & 31u);
     const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n_tuples; m += gstride) {
-        const uint32_t *p = w + m * stride;
-        uint32_t cell = 0u;
-        for (uint32_t i = 0; i < t; ++i) cell = (cell << bits) | ((__ldg(p + i) >> shift) & mask);
-        atomicAdd(&hist[cell], 1u);
+    for (uint64_t m0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m0 < n_tuples; m0 += kTupleUnroll * gstride) {
+        uint32_t cell[kTupleUnroll];
+#pragma unroll
+        for (int j = 0; j < kTupleUnroll; ++j) cell[j] = 0u;
+        for (uint32_t i = 0; i < t; ++i) {
+#pragma unroll
+            for (int j = 0; j < kTupleUnroll; ++j) {
+                const uint64_t m = m0 + j * gstride;
+                const uint32_t x = m < n_tuples ? __ldg(w + m * stride + i) : 0u;
+                cell[j] = (cell[j] << bits) | ((x >> shift) & mask);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kTupleUnroll; ++j)
+            if (m0 + j * gstride < n_tuples) atomicAdd(&hist[cell[j] * LANES + col], 1u);
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < cells; i += blockDim.x)
-        if (hist[i]) atomicAdd(&counts[i], (unsigned long long)hist[i]);
+    for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) {
+        unsigned long long v = 0;
+        for (uint32_t l = 0; l < (uint32_t)LANES; ++l) v += hist[c * LANES + l];
+        if (v) atomicAdd(&counts[c], v);
+    }
 }
 
 // ----------------------------------------------------------------- gaps
 
 constexpr uint32_t kGapSpan = 8192;  // words per warp span (256 steps of 32)
+constexpr int kGapUnroll = 4;        // steps whose loads are issued together
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 __device__ __forceinline__ bool gap_hit(uint32_t x, uint64_t lo, uint64_t hi)
@@ -117,22 +143,29 @@ __global__ void __launch_bounds__(256) gap_span_kernel(const uint32_t *__restric
     for (uint64_t sp = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); sp < n_spans; sp += warps) {
         const uint64_t start = sp * kGapSpan;
         uint32_t first = kNone, last = kNone;  // span-local offsets, warp-uniform
-        for (uint32_t it = 0; it < kGapSpan / 32; ++it) {
-            const uint64_t base = start + (uint64_t)it * 32;
-            if (base >= n) break;
-            const uint64_t idx = base + lane;
-            const bool hit = idx < n && gap_hit(__ldg(w + idx), lo, hi);
-            const uint32_t mask = __ballot_sync(0xFFFFFFFFu, hit);
-            if (hit) {
-                const uint32_t below = mask & ((1u << lane) - 1u);
-                uint32_t gap = kNone;
-                if (below) gap = lane - (31u - __clz(below)) - 1u;
-                else if (last != kNone) gap = it * 32 + lane - last - 1u;
-                if (gap != kNone) atomicAdd(&hist[min(gap, t_max)], 1u);
+        for (uint32_t it0 = 0; it0 < kGapSpan / 32; it0 += kGapUnroll) {
+            if (start + (uint64_t)it0 * 32 >= n) break;
+            bool hits[kGapUnroll];
+#pragma unroll
+            for (int u = 0; u < kGapUnroll; ++u) {  // loads for the next kGapUnroll steps first
+                const uint64_t idx = start + (uint64_t)(it0 + u) * 32 + lane;
+                hits[u] = idx < n && gap_hit(__ldg(w + idx), lo, hi);
             }
-            if (mask) {
-                if (first == kNone) first = it * 32 + (__ffs(mask) - 1);
-                last = it * 32 + (31u - __clz(mask));
+#pragma unroll
+            for (int u = 0; u < kGapUnroll; ++u) {
+                const uint32_t it = it0 + u;
+                const uint32_t mask = __ballot_sync(0xFFFFFFFFu, hits[u]);
+                if (hits[u]) {
+                    const uint32_t below = mask & ((1u << lane) - 1u);
+                    uint32_t gap = kNone;
+                    if (below) gap = lane - (31u - __clz(below)) - 1u;
+                    else if (last != kNone) gap = it * 32 + lane - last - 1u;
+                    if (gap != kNone) atomicAdd(&hist[min(gap, t_max)], 1u);
+                }
+                if (mask) {
+                    if (first == kNone) first = it * 32 + (__ffs(mask) - 1);
+                    last = it * 32 + (31u - __clz(mask));
+                }
             }
         }
         if (lane == 0) {
@@ -186,18 +219,30 @@ __global__ void gap_carry_kernel(const uint32_t *__restrict__ span_last, uint64_
 }
 
 // ------------------------------------------------------------- birthday
+//
+// Per sample (one CTA): the n birthdays are sorted by a counting sort on
+// their top log2(n) bits (one shared-memory atomic per key gives both the
+// bucket count and the key's rank inside its bucket), a block scan of the
+// bucket counts, a scatter, and insertion sorts inside the buckets, which
+// hold about one key each.  A sample with a bucket of more than
+// kMaxBucket keys (a very non-uniform stream) is sorted by a bitonic
+// network instead, so the work stays bounded.  R is then n minus the number
+// of distinct spacings (equal values are adjacent once sorted), counted by
+// inserting the spacings into a shared-memory hash set: no second sort.
 
 constexpr int kBirthdayBlock = 512;
+constexpr uint32_t kMaxBucket = 64;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 // Ascending bitonic sort of y[0..n) (n a power of two) by the whole block.
-__device__ __forceinline__ void block_bitonic_sort(unsigned long long *y, uint32_t n)
+__device__ __forceinline__ void block_bitonic_sort(uint32_t *y, uint32_t n)
 {
     for (uint32_t k = 2; k <= n; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
             for (uint32_t p = threadIdx.x; p < n / 2; p += blockDim.x) {
                 const uint32_t lo = ((p & ~(j - 1)) << 1) | (p & (j - 1));
                 const uint32_t hi = lo + j;
-                const unsigned long long a = y[lo], b = y[hi];
+                const uint32_t a = y[lo], b = y[hi];
                 if ((a > b) == ((lo & k) == 0)) {
                     y[lo] = b;
                     y[hi] = a;
@@ -208,45 +253,150 @@ __device__ __forceinline__ void block_bitonic_sort(unsigned long long *y, uint32
     }
 }
 
-__global__ void __launch_bounds__(kBirthdayBlock) birthday_kernel(const uint32_t *__restrict__ w, uint64_t n_samples,
+// Exclusive prefix sum of c[0..nb) in place (nb a power of two <= 4096), by
+// the whole block; each thread scans a run of nb / blockDim entries (read
+// and written as 16-byte vectors when the run allows).
+__device__ __forceinline__ void block_exclusive_scan(uint32_t *c, uint32_t nb, uint32_t *warp_tot)
+{
+    const uint32_t T = blockDim.x;
+    const uint32_t per = (nb + T - 1) / T;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t b0 = threadIdx.x * per;
+    uint32_t v[8];  // per <= 8 (nb <= 4096, blockDim >= 512 when nb > 2048)
+    if (per == 8) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(c + b0), b = *reinterpret_cast<const uint4 *>(c + b0 + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+        for (uint32_t i = 0; i < 8; ++i) v[i] = (i < per && b0 + i < nb) ? c[b0 + i] : 0u;
+    }
+    uint32_t run = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) run += v[i];
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += x;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t acc = incl - run;
+    for (uint32_t w = 0; w < warp; ++w) acc += warp_tot[w];
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) {
+        const uint32_t x = v[i];
+        v[i] = acc;
+        acc += x;
+    }
+    if (per == 8) {
+        *reinterpret_cast<uint4 *>(c + b0) = make_uint4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<uint4 *>(c + b0 + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+        for (uint32_t i = 0; i < 8; ++i)
+            if (i < per && b0 + i < nb) c[b0 + i] = v[i];
+    }
+    __syncthreads();
+}
+
+// Insert v into the hash set tab (tsize slots, a power of two); returns 1
+// when v was not there yet.  The set never fills (tsize = 2n), so the probe
+// ends.
+__device__ __forceinline__ uint32_t set_insert(uint32_t *tab, uint32_t tbits, uint32_t v)
+{
+    uint32_t h = (v * 0x9E3779B1u) >> (32 - tbits);
+    const uint32_t mask = (1u << tbits) - 1u;
+    for (;;) {
+        const uint32_t old = atomicCAS(&tab[h], kEmpty, v);
+        if (old == kEmpty) return 1u;
+        if (old == v) return 0u;
+        h = (h + 1u) & mask;
+    }
+}
+
+__global__ void __launch_bounds__(kBirthdayBlock, 3) birthday_kernel(const uint32_t *__restrict__ w, uint64_t n_samples,
                                                                   uint32_t log2_n, uint32_t bits, uint32_t shift,
                                                                   uint32_t r_max,
                                                                   unsigned long long *__restrict__ counts)
 {
-    extern __shared__ unsigned long long y[];
-    __shared__ uint32_t red[kBirthdayBlock / 32];
+    extern __shared__ uint32_t smem[];
+    __shared__ uint32_t warp_tot[kBirthdayBlock / 32];
+    __shared__ uint32_t flags;  // bit 0: a spacing of 2^32 - 1; bit 1: one of 2^32
     const uint32_t n = 1u << log2_n;
-    const unsigned long long m = 1ull << bits;
-    const unsigned long long mask = m - 1ull;
+    const uint32_t lb = log2_n < bits ? log2_n : bits;  // bucket bits
+    const uint32_t nb = 1u << lb;
+    const uint32_t tbits = log2_n + 1;                  // hash set of 2n slots
+    uint32_t *keys = smem;                              // n
+    uint32_t *cnt = keys + n;                           // nb <= n; dead once the keys are sorted,
+    uint32_t *tab = cnt;                                // then the same 2n words hold the hash set
+    const uint32_t mask = bits == 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
+    const uint64_t m = 1ull << bits;
     constexpr uint32_t kMaxPer = 4096 / kBirthdayBlock;
     for (uint64_t q = blockIdx.x; q < n_samples; q += gridDim.x) {
-        const uint32_t *p = w + q * n;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) y[i] = ((unsigned long long)__ldg(p + i) >> shift) & mask;
-        __syncthreads();
-        block_bitonic_sort(y, n);
-        unsigned long long sp[kMaxPer];
+        uint32_t y[kMaxPer], rank[kMaxPer];
 #pragma unroll
         for (uint32_t k = 0; k < kMaxPer; ++k) {
             const uint32_t i = threadIdx.x + k * blockDim.x;
-            if (i < n) sp[k] = (i + 1 < n) ? y[i + 1] - y[i] : y[0] + m - y[n - 1];
+            if (i < n) y[k] = (__ldg(w + q * n + i) >> shift) & mask;
         }
+        for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) cnt[i] = 0u;
+        if (threadIdx.x == 0) flags = 0u;
         __syncthreads();
+        bool big = false;
 #pragma unroll
         for (uint32_t k = 0; k < kMaxPer; ++k) {
             const uint32_t i = threadIdx.x + k * blockDim.x;
-            if (i < n) y[i] = sp[k];
+            if (i < n) {
+                rank[k] = atomicAdd(&cnt[y[k] >> (bits - lb)], 1u);
+                big |= rank[k] >= kMaxBucket;
+            }
         }
-        __syncthreads();
-        block_bitonic_sort(y, n);
-        uint32_t r = 0;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) r += (i > 0 && y[i] == y[i - 1]) ? 1u : 0u;
+        if (__syncthreads_or(big)) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xFFFFFFFFu, r, o);
-        if ((threadIdx.x & 31u) == 0) red[threadIdx.x >> 5] = r;
+            for (uint32_t k = 0; k < kMaxPer; ++k) {
+                const uint32_t i = threadIdx.x + k * blockDim.x;
+                if (i < n) keys[i] = y[k];
+            }
+            __syncthreads();
+            block_bitonic_sort(keys, n);
+        } else {
+            block_exclusive_scan(cnt, nb, warp_tot);
+#pragma unroll
+            for (uint32_t k = 0; k < kMaxPer; ++k) {
+                const uint32_t i = threadIdx.x + k * blockDim.x;
+                if (i < n) keys[cnt[y[k] >> (bits - lb)] + rank[k]] = y[k];
+            }
+            __syncthreads();
+            for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+                const uint32_t s0 = cnt[b], s1 = b + 1 < nb ? cnt[b + 1] : n;
+                for (uint32_t i = s0 + 1; i < s1; ++i) {  // insertion sort, <= kMaxBucket keys
+                    const uint32_t v = keys[i];
+                    uint32_t j = i;
+                    while (j > s0 && keys[j - 1] > v) {
+                        keys[j] = keys[j - 1];
+                        --j;
+                    }
+                    keys[j] = v;
+                }
+            }
+            __syncthreads();
+        }
+        for (uint32_t i = threadIdx.x; i < 2 * n; i += blockDim.x) tab[i] = kEmpty;
+        __syncthreads();
+        uint32_t distinct = 0;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t v = i + 1 < n ? (uint64_t)keys[i + 1] - keys[i] : (uint64_t)keys[0] + m - keys[n - 1];
+            if (v == 0xFFFFFFFFull) atomicOr(&flags, 1u);
+            else if (v == (1ull << 32)) atomicOr(&flags, 2u);
+            else distinct += set_insert(tab, tbits, (uint32_t)v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) distinct += __shfl_down_sync(0xFFFFFFFFu, distinct, o);
+        if ((threadIdx.x & 31u) == 0) warp_tot[threadIdx.x >> 5] = distinct;
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint32_t R = 0;
-            for (uint32_t i = 0; i < blockDim.x / 32; ++i) R += red[i];
+            uint32_t d = __popc(flags);
+            for (uint32_t i = 0; i < blockDim.x / 32; ++i) d += warp_tot[i];
+            const uint32_t R = n - d;
             atomicAdd(&counts[R < r_max ? R : r_max], 1ull);
         }
         __syncthreads();
@@ -312,16 +462,23 @@ orand_status_t orand_stat_tuples(const uint32_t *words, uint64_t n_words, uint32
     DeviceInfo info;
     if ((st = current_device(&info)) != ORAND_OK) return st;
     const uint32_t cells = 1u << (t * bits);
-    const size_t smem = (size_t)cells * sizeof(uint32_t);
-    if (smem > 48 * 1024)
-        ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const bool lanes = cells <= 256;
+    const size_t smem = (size_t)cells * (lanes ? 32 : 1) * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        if (lanes) ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     // Per-CTA u32 counters: launch pieces small enough that no CTA passes 2^31.
     const uint64_t piece = 1ull << 36;
     for (uint64_t m0 = 0; m0 < n_tuples; m0 += piece) {
         const uint64_t nt = n_tuples - m0 < piece ? n_tuples - m0 : piece;
         const unsigned grid = grid_for(nt, 256, info.sm_count, 4);
-        tuple_kernel<<<grid, 256, smem, stream>>>(words + m0 * stride, nt, t, bits, shift, stride, cells,
-                                                  (unsigned long long *)counts);
+        if (lanes)
+            tuple_kernel<32><<<grid, 256, smem, stream>>>(words + m0 * stride, nt, t, bits, shift, stride, cells,
+                                                         (unsigned long long *)counts);
+        else
+            tuple_kernel<1><<<grid, 256, smem, stream>>>(words + m0 * stride, nt, t, bits, shift, stride, cells,
+                                                        (unsigned long long *)counts);
         if ((st = launch_status()) != ORAND_OK) return st;
     }
     return ORAND_OK;
@@ -368,8 +525,15 @@ orand_status_t orand_stat_birthday(const uint32_t *words, uint64_t n_words, uint
     if ((st = current_device(&info)) != ORAND_OK) return st;
     const uint32_t n = 1u << log2_n;
     const unsigned block = n / 2 < (uint32_t)kBirthdayBlock ? (n / 2 < 32 ? 32 : n / 2) : kBirthdayBlock;
-    const size_t smem = (size_t)n * sizeof(unsigned long long);
-    const unsigned grid = (unsigned)(n_samples < (uint64_t)info.sm_count * 4 ? n_samples : (uint64_t)info.sm_count * 4);
+    const size_t smem = (size_t)3 * n * sizeof(uint32_t);  // keys (n), bucket counts then hash set (2n)
+    // The kernel's static shared memory comes on top: opt in whenever the
+    // dynamic part reaches the 48 KB default.
+    if (smem >= 48 * 1024)
+        ORAND_CUDA_TRY(cudaFuncSetAttribute(birthday_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;  // one wave: as many CTAs as fit at once
+    ORAND_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, birthday_kernel, (int)block, smem));
+    const uint64_t wave = (uint64_t)info.sm_count * (per_sm > 0 ? per_sm : 1);
+    const unsigned grid = (unsigned)(n_samples < wave ? n_samples : wave);
     birthday_kernel<<<grid, block, smem, stream>>>(words, n_samples, log2_n, bits, shift, r_max,
                                                    (unsigned long long *)counts);
     return launch_status();

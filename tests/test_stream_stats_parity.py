@@ -162,3 +162,22 @@ def test_battery_rejects_planted_correlation(torch_cuda):
         verdicts[name] = ST.evaluate(kind, prm, c.cpu().numpy())["verdict"]
     assert verdicts["triples_hi4"] == "fail" and verdicts["birthday_4096_2p32"] == "fail"
     torch.cuda.synchronize()
+
+
+def test_birthday_extreme_spacings(torch_cuda):
+    """Spacings of exactly 2^32 - 1 (the hash set's empty marker) and 2^32
+    (the wrap spacing when all birthdays are equal), in 32-bit years."""
+    M = 0xFFFFFFFF
+    samples = [[0, M, M, M], [0, M, 0, M], [0, M, 5, 7], [M, M, M, M], [0, 1, 2, 3], [M, 0, 1, M - 1]]
+    w = np.array([x for s in samples for x in s], np.uint32)
+    c = orand.stat_birthday(dev_words(torch_cuda, w), 2, 32, 0, 8)
+    assert np.array_equal(c.cpu().numpy().astype(np.uint64), S.birthday_counts(w, 2, 32, 0, 8))
+
+
+def test_birthday_bucket_overflow_falls_back(torch_cuda):
+    """A sample whose birthdays crowd into few buckets (only the low 12 bits
+    vary) takes the bounded fallback sort; counts still equal the oracle's."""
+    rng = np.random.default_rng(8)
+    w = (rng.integers(0, 4096, size=4096 * 6, dtype=np.uint64).astype(np.uint32) | np.uint32(0x5A5A0000))
+    c = orand.stat_birthday(dev_words(torch_cuda, w), 12, 32, 0, 4096)
+    assert np.array_equal(c.cpu().numpy().astype(np.uint64), S.birthday_counts(w, 12, 32, 0, 4096))
