@@ -597,6 +597,13 @@ def main():
         baselines["ragged/one_launch_per_request_first2000"] = ragged_serial_baseline(torch, orand, W)
         baselines["curand_philox4_32_10_2^28_values"] = curand_reference(torch)
         baselines["paper_brownian_dynamics_1e6x1e4"] = paper_brownian_benchmark(torch, orand)
+        from paper_2310_19925_b300 import host_bench
+
+        hb = host_bench.run()
+        hb["note"] = "paper §5 host micro-benchmark: one host thread, fresh generator per stream, vs std::mt19937"
+        baselines["host_microbench_ns_per_word"] = {"lengths": hb["lengths"], **hb["ns_per_word"],
+                                                    "speedup_vs_mt19937": hb["speedup_vs_mt19937"],
+                                                    "note": hb["note"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -35,6 +35,11 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 
+/* The generator cores (round functions, key schedules, the engines' word
+ * draws) compile for the host too, so a CPU program gets the same streams
+ * from the same source; the value maps are device-only. */
+#define ORAND_HD __host__ __device__ __forceinline__
+
 namespace orand {
 
 /* ---------------------------------------------------------------- Philox */
@@ -46,7 +51,7 @@ constexpr uint32_t PHILOX_W1 = 0xBB67AE85u;  /* floor(2^32 (sqrt(3) - 1)) */
 
 /* One Philox round on (c0..c3) with round key (k0, k1).  The 64-bit
  * products map to one wide integer multiply-add each. */
-__device__ __forceinline__ void philox_round(uint32_t &c0, uint32_t &c1, uint32_t &c2,
+ORAND_HD void philox_round(uint32_t &c0, uint32_t &c1, uint32_t &c2,
                                              uint32_t &c3, uint32_t k0, uint32_t k1)
 {
     const uint64_t p0 = (uint64_t)PHILOX_M0 * c0;
@@ -60,7 +65,7 @@ __device__ __forceinline__ void philox_round(uint32_t &c0, uint32_t &c1, uint32_
 }
 
 /* Stateless Philox4x32-10 block function. */
-__device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key)
+ORAND_HD uint4 philox4x32_10(uint4 ctr, uint2 key)
 {
     uint32_t c0 = ctr.x, c1 = ctr.y, c2 = ctr.z, c3 = ctr.w;
     uint32_t k0 = key.x, k1 = key.y;
@@ -76,7 +81,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key)
  * thread reuses them for every block of the same key). */
 struct PhiloxKeys {
     uint32_t k0[10], k1[10];
-    __device__ __forceinline__ explicit PhiloxKeys(uint64_t key64)
+    ORAND_HD explicit PhiloxKeys(uint64_t key64)
     {
         uint32_t a = (uint32_t)key64, b = (uint32_t)(key64 >> 32);
 #pragma unroll
@@ -85,7 +90,7 @@ struct PhiloxKeys {
             a += PHILOX_W0; b += PHILOX_W1;
         }
     }
-    __device__ __forceinline__ uint4 block(uint32_t b_idx, uint32_t counter) const
+    ORAND_HD uint4 block(uint32_t b_idx, uint32_t counter) const
     {
         uint32_t c0 = b_idx, c1 = counter, c2 = 0u, c3 = 0u;
 #pragma unroll
@@ -94,7 +99,7 @@ struct PhiloxKeys {
     }
 };
 
-__device__ __forceinline__ uint4 philox_block(uint64_t key64, uint32_t counter, uint32_t b_idx)
+ORAND_HD uint4 philox_block(uint64_t key64, uint32_t counter, uint32_t b_idx)
 {
     return philox4x32_10(make_uint4(b_idx, counter, 0u, 0u),
                          make_uint2((uint32_t)key64, (uint32_t)(key64 >> 32)));
@@ -102,10 +107,17 @@ __device__ __forceinline__ uint4 philox_block(uint64_t key64, uint32_t counter, 
 
 /* -------------------------------------------------------------- Threefry */
 
-__device__ __forceinline__ uint32_t rotl32(uint32_t x, int r) { return __funnelshift_l(x, x, r); }
+ORAND_HD uint32_t rotl32(uint32_t x, int r)
+{
+#ifdef __CUDA_ARCH__
+    return __funnelshift_l(x, x, r);
+#else
+    return (x << r) | (x >> ((32 - r) & 31));
+#endif
+}
 
 template <int RA, int RB, bool EVEN>
-__device__ __forceinline__ void threefry_round(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3)
+ORAND_HD void threefry_round(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3)
 {
     if (EVEN) {
         x0 += x1; x1 = rotl32(x1, RA) ^ x0;
@@ -118,7 +130,7 @@ __device__ __forceinline__ void threefry_round(uint32_t &x0, uint32_t &x1, uint3
 
 /* Four rounds starting at row R0 of the rotation table, then injection I. */
 template <int R0, int I>
-__device__ __forceinline__ void threefry_quad(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
+ORAND_HD void threefry_quad(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
                                               const uint32_t ks[5])
 {
     constexpr int ROT[8][2] = {{10, 26}, {11, 21}, {13, 27}, {23, 5},
@@ -134,7 +146,7 @@ __device__ __forceinline__ void threefry_quad(uint32_t &x0, uint32_t &x1, uint32
 }
 
 /* Stateless Threefry4x32-20 block function. */
-__device__ __forceinline__ uint4 threefry4x32_20(uint4 ctr, uint4 key)
+ORAND_HD uint4 threefry4x32_20(uint4 ctr, uint4 key)
 {
     uint32_t ks[5];
     ks[0] = key.x; ks[1] = key.y; ks[2] = key.z; ks[3] = key.w;
@@ -148,7 +160,7 @@ __device__ __forceinline__ uint4 threefry4x32_20(uint4 ctr, uint4 key)
     return make_uint4(x0, x1, x2, x3);
 }
 
-__device__ __forceinline__ uint4 threefry_block(uint64_t key64, uint32_t counter, uint32_t b_idx)
+ORAND_HD uint4 threefry_block(uint64_t key64, uint32_t counter, uint32_t b_idx)
 {
     return threefry4x32_20(make_uint4(b_idx, counter, 0u, 0u),
                            make_uint4((uint32_t)key64, (uint32_t)(key64 >> 32), 0u, 0u));
@@ -156,19 +168,24 @@ __device__ __forceinline__ uint4 threefry_block(uint64_t key64, uint32_t counter
 
 /* --------------------------------------------------------------- Squares */
 
-/* x*x + y modulo 2^64 from 32-bit halves: one wide multiply-add for the low
- * product plus y, one multiply-add for the cross term 2*xl*xh. */
-__device__ __forceinline__ uint64_t sq_add(uint64_t x, uint64_t y)
+/* x*x + y modulo 2^64.  On the GPU from 32-bit halves: one wide
+ * multiply-add for the low product plus y, one multiply-add for the cross
+ * term 2*xl*xh (xh^2 only reaches bit 64 and above). */
+ORAND_HD uint64_t sq_add(uint64_t x, uint64_t y)
 {
+#ifdef __CUDA_ARCH__
     const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
     const uint64_t p = (uint64_t)xl * xl + y;
     const uint32_t hi = (uint32_t)(p >> 32) + xl * (xh << 1);
     return ((uint64_t)hi << 32) | (uint32_t)p;
+#else
+    return x * x + y;  /* the same value: a CPU multiplies 64 bits at once */
+#endif
 }
 
-__device__ __forceinline__ uint64_t swap_halves(uint64_t v) { return (v >> 32) | (v << 32); }
+ORAND_HD uint64_t swap_halves(uint64_t v) { return (v >> 32) | (v << 32); }
 
-__device__ __forceinline__ uint32_t squares32(uint64_t ctr, uint64_t key)
+ORAND_HD uint32_t squares32(uint64_t ctr, uint64_t key)
 {
     uint64_t x = ctr * key;
     const uint64_t y = x, z = y + key;
@@ -179,7 +196,7 @@ __device__ __forceinline__ uint32_t squares32(uint64_t ctr, uint64_t key)
 }
 
 /* Per-stream Squares key: MurmurHash3's 64-bit finaliser, forced odd. */
-__device__ __forceinline__ uint64_t squares_key(uint64_t key64)
+ORAND_HD uint64_t squares_key(uint64_t key64)
 {
     uint64_t h = key64;
     h ^= h >> 33;
@@ -191,7 +208,7 @@ __device__ __forceinline__ uint64_t squares_key(uint64_t key64)
 }
 
 /* Four consecutive Squares words 4b..4b+3 of stream (key, counter). */
-__device__ __forceinline__ uint4 squares_block(uint64_t sq_key, uint32_t counter, uint32_t b_idx)
+ORAND_HD uint4 squares_block(uint64_t sq_key, uint32_t counter, uint32_t b_idx)
 {
     const uint64_t base = ((uint64_t)counter << 32) | ((uint64_t)b_idx << 2);
     return make_uint4(squares32(base, sq_key), squares32(base + 1, sq_key),
@@ -204,15 +221,22 @@ struct TycheState {
     uint32_t a, b, c, d;
 };
 
-__device__ __forceinline__ void tyche_mix(TycheState &s)
+ORAND_HD void tyche_mix(TycheState &s)
 {
+#ifdef __CUDA_ARCH__
     s.a += s.b; s.d = __byte_perm(s.d ^ s.a, 0, 0x1032);   /* rotl 16 */
     s.c += s.d; s.b = rotl32(s.b ^ s.c, 12);
     s.a += s.b; s.d = __byte_perm(s.d ^ s.a, 0, 0x2103);   /* rotl 8 */
     s.c += s.d; s.b = rotl32(s.b ^ s.c, 7);
+#else
+    s.a += s.b; s.d = rotl32(s.d ^ s.a, 16);
+    s.c += s.d; s.b = rotl32(s.b ^ s.c, 12);
+    s.a += s.b; s.d = rotl32(s.d ^ s.a, 8);
+    s.c += s.d; s.b = rotl32(s.b ^ s.c, 7);
+#endif
 }
 
-__device__ __forceinline__ TycheState tyche_init(uint64_t key64, uint32_t counter)
+ORAND_HD TycheState tyche_init(uint64_t key64, uint32_t counter)
 {
     TycheState s;
     s.a = (uint32_t)(key64 >> 32);
@@ -224,7 +248,7 @@ __device__ __forceinline__ TycheState tyche_init(uint64_t key64, uint32_t counte
     return s;
 }
 
-__device__ __forceinline__ uint32_t tyche_next(TycheState &s)
+ORAND_HD uint32_t tyche_next(TycheState &s)
 {
     tyche_mix(s);
     return s.b;
@@ -395,9 +419,9 @@ __device__ __forceinline__ float box_muller_cos_f32(uint32_t w0, uint32_t w1)
  * generators keep a 4-word buffer; Tyche keeps its 4-word state. */
 class Philox {
   public:
-    __device__ __forceinline__ Philox(uint64_t seed, uint32_t counter)
+    ORAND_HD Philox(uint64_t seed, uint32_t counter)
         : key_(seed), counter_(counter), blk_(0), lane_(4) {}
-    __device__ __forceinline__ uint32_t operator()()
+    ORAND_HD uint32_t operator()()
     {
         if (lane_ == 4) { buf_ = philox_block(key_, counter_, blk_++); lane_ = 0; }
         const uint32_t w = lane_ == 0 ? buf_.x : lane_ == 1 ? buf_.y : lane_ == 2 ? buf_.z : buf_.w;
@@ -418,9 +442,9 @@ class Philox {
 
 class Threefry {
   public:
-    __device__ __forceinline__ Threefry(uint64_t seed, uint32_t counter)
+    ORAND_HD Threefry(uint64_t seed, uint32_t counter)
         : key_(seed), counter_(counter), blk_(0), lane_(4) {}
-    __device__ __forceinline__ uint32_t operator()()
+    ORAND_HD uint32_t operator()()
     {
         if (lane_ == 4) { buf_ = threefry_block(key_, counter_, blk_++); lane_ = 0; }
         const uint32_t w = lane_ == 0 ? buf_.x : lane_ == 1 ? buf_.y : lane_ == 2 ? buf_.z : buf_.w;
@@ -439,9 +463,9 @@ class Threefry {
 
 class Squares {
   public:
-    __device__ __forceinline__ Squares(uint64_t seed, uint32_t counter)
+    ORAND_HD Squares(uint64_t seed, uint32_t counter)
         : key_(squares_key(seed)), ctr_((uint64_t)counter << 32) {}
-    __device__ __forceinline__ uint32_t operator()() { return squares32(ctr_++, key_); }
+    ORAND_HD uint32_t operator()() { return squares32(ctr_++, key_); }
     __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
     __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
     __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
@@ -452,8 +476,8 @@ class Squares {
 
 class Tyche {
   public:
-    __device__ __forceinline__ Tyche(uint64_t seed, uint32_t counter) : s_(tyche_init(seed, counter)) {}
-    __device__ __forceinline__ uint32_t operator()() { return tyche_next(s_); }
+    ORAND_HD Tyche(uint64_t seed, uint32_t counter) : s_(tyche_init(seed, counter)) {}
+    ORAND_HD uint32_t operator()() { return tyche_next(s_); }
     __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
     __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
     __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }

@@ -77,6 +77,8 @@ _SIGS = {
     "orand_stat_tuples": (_i32, [_vp, _u64, _u32, _u32, _u32, _u32, _vp, _vp]),
     "orand_stat_gaps": (_i32, [_vp, _vp, _u64, _u64, _u64, _u32, _vp, _vp, _vp]),
     "orand_stat_birthday": (_i32, [_vp, _u64, _u32, _u32, _u32, _u32, _vp, _vp]),
+    "orand_host_fill_u32": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp]),
+    "orand_host_microbench": (_i32, [_i32, _vp, _u32, _u64, _vp, _vp]),
     "orand_fill_ragged_serial": (_i32, [_vp, _sz, _vp, _u64, _vp]),
     "orand_ragged_set_config": (_i32, [_vp, _vp]),
     "orand_ragged_get_config": (_i32, [_vp, _vp]),
@@ -332,6 +334,34 @@ def stat_birthday(words, log2_n, bits, shift, r_max, counts=None, stream=None):
     orand_stat_birthday(_ptr(w) if w.numel() else 0, w.numel(), log2_n, bits, shift, r_max, _ptr(c),
                         _stream_handle(stream))
     return c
+
+
+# ------------------------------------------------------------------- host --
+
+HOST_MT19937 = 100
+
+
+def host_fill_u32(gen, seed, counter, n_streams, draws_per_stream):
+    """The u32 fill computed on the host (numpy uint32 array); same bits as
+    orand_fill_u32 on the GPU."""
+    import numpy as np
+
+    out = np.empty(n_streams * draws_per_stream, dtype=np.uint32)
+    _check(_lib().orand_host_fill_u32(gen, seed & (2**64 - 1), counter & 0xFFFFFFFF, n_streams, draws_per_stream,
+                                      out.ctypes.data if out.size else None), "orand_host_fill_u32")
+    return out
+
+
+def host_microbench(gen, lengths, words_per_length=1 << 22):
+    """ns per stream for each stream length (the paper's host micro-benchmark)."""
+    import numpy as np
+
+    L = np.ascontiguousarray(lengths, dtype=np.uint64)
+    ns = np.zeros(L.size, dtype=np.float64)
+    sink = np.zeros(1, dtype=np.uint32)
+    _check(_lib().orand_host_microbench(gen, L.ctypes.data, L.size, words_per_length, ns.ctypes.data,
+                                        sink.ctypes.data), "orand_host_microbench")
+    return ns
 
 
 # ------------------------------------------------------------------ walks --
