@@ -37,6 +37,16 @@ HEAD_KERNEL_SOURCES = ["paper_2310_19925_b300/csrc/fill.cu", "paper_2310_19925_b
                        "paper_2310_19925_b300/csrc/common.cuh", "include/orand_device.cuh"]
 METRIC = "Philox u32 fill GB/s vs HBM peak; walk particle-steps/s; adjoint vs plain walk"
 
+# Issue peak of the integer/FP32 pipes: 148 SMs x 4 schedulers x 32 lanes x
+# 2.032 GHz (the B300's unit counts and maximum SM clock), in lane-operations/s.
+ALU_PEAK = 148 * 128 * 2.032e9
+# Algorithmic operations per 2D particle-step, counted from the kernel source:
+# Philox4x32-10 with the two used words and the constant counter words
+# folded (33), the Box-Muller radius (34) and sin/cos pair (29), the step
+# scale (1), two FMA sums (2), the step loop shared by two particles (1.5),
+# and the Kahan add of each 16-step block sum (0.5).
+WALK2D_OPS_PER_STEP = 101
+
 
 def parse_args():
     ap = argparse.ArgumentParser()
@@ -557,9 +567,11 @@ def main():
     traffic = ncu_traffic(HEAD_KERNEL_KEY, src)
 
     row_table = {}
+    step_ms = total_ms / args.steps
     for r in rows:
         t = max_over_ranks(statistics.mean(r.times_ms))
-        e = {"ms": round(t, 4), r.unit + "_per_s": world * r.units / (t * 1e-3)}
+        e = {"ms": round(t, 4), r.unit + "_per_s": world * r.units / (t * 1e-3),
+             "share_of_step": round(statistics.mean(r.times_ms) / step_ms, 4)}
         if r.bytes_written:
             e["GB/s"] = round(world * r.bytes_written / (t * 1e-3) / 1e9, 1)
             e["frac_hbm"] = round(r.bytes_written / (t * 1e-3) / 1e9 / peak, 4)
@@ -567,6 +579,19 @@ def main():
         if hasattr(r, "finish"):
             e.update(r.finish())
         row_table[r.name] = e
+
+    # Per-kernel rooflines beside the headline: the step's dominant kernel
+    # (the 2D walk, issue-bound) against the issue peak.
+    rooflines = {}
+    w2 = row_table.get("walk2d/fused")
+    if w2:
+        ops = w2["particle-steps_per_s"] / world * WALK2D_OPS_PER_STEP
+        rooflines["walk2d_kernel"] = {"bound": "alu", "achieved": ops, "peak": ALU_PEAK, "unit": "lane-ops/s",
+                                      "frac": ops / ALU_PEAK, "ops_per_particle_step": WALK2D_OPS_PER_STEP,
+                                      "share_of_step": w2["share_of_step"],
+                                      "peak_kind": "derived: 148 SMs x 128 lanes x 2.032 GHz"}
+    rooflines["fill_tile_kernel<philox,u32>"] = {"bound": "hbm", "frac": achieved / peak,
+                                                 "share_of_step": row_table[head.name]["share_of_step"]}
 
     # End to end through the C ABI: the same fill, then the 1 GiB result read
     # back into pinned host memory, both inside the timed region.
@@ -625,6 +650,7 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "fill_tile_kernel<philox4x32_10, u32, R=4> (TMA tile store)",
                          "peak_kind": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"},
+            "rooflines": rooflines,
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": sum(r.kernels for r in rows) * args.steps,
