@@ -45,6 +45,7 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--max-log2", type=int, default=20)
     ap.add_argument("--length", type=int, default=1 << 20)
+    ap.add_argument("--kappa", type=float, default=0.0, help="walk3d: OU drift mu - kappa x")
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
 
@@ -69,8 +70,9 @@ def main(argv=None):
         res.update(particles=args.particles, steps=args.steps, ms=statistics.mean(ts),
                    particle_steps_per_s=args.particles * args.steps / (statistics.mean(ts) * 1e-3))
     elif args.case == "walk3d":
-        prm = orand.walk3d_params(args.particles, args.steps)
+        prm = orand.walk3d_params(args.particles, args.steps, kappa=args.kappa)
         ctx = orand.default_context().handle
+        dk = torch.empty((), dtype=torch.float64, device="cuda")
         xT = torch.empty((args.particles, 3), dtype=torch.float32, device="cuda")
         ck = torch.empty((orand.n_checkpoints(args.steps, 64), args.particles, 3), dtype=torch.float32,
                          device="cuda")
@@ -80,11 +82,11 @@ def main(argv=None):
 
         def fn():
             orand.orand_walk3d_fwd(ctx, prm, 0, xT.data_ptr(), ck.data_ptr(), loss.data_ptr(), sh)
-            orand.orand_walk3d_bwd(ctx, prm, xT.data_ptr(), ck.data_ptr(), 0, g.data_ptr(), g.data_ptr() + 24, 0,
-                                   dx0.data_ptr(), sh)
+            orand.orand_walk3d_bwd(ctx, prm, xT.data_ptr(), ck.data_ptr(), 0, g.data_ptr(), g.data_ptr() + 24,
+                                   dk.data_ptr() if args.kappa else 0, dx0.data_ptr(), sh)
 
         ts = timed(torch, fn, args.reps)
-        res.update(particles=args.particles, steps=args.steps, ms=statistics.mean(ts),
+        res.update(particles=args.particles, steps=args.steps, kappa=args.kappa, ms=statistics.mean(ts),
                    particle_steps_per_s=args.particles * args.steps / (statistics.mean(ts) * 1e-3))
     elif args.case in ("ragged", "tyche-chain"):
         if args.case == "ragged":

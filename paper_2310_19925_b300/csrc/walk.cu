@@ -199,6 +199,12 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_init_kernel(Walk3dArgs a, f
     x0[3 * i + 2] = x[2];
 }
 
+// Forward walk.  Increments are summed in FP32 over blocks of at most
+// kSumBlock steps (a block also ends at each checkpoint) and each block sum
+// is Kahan-added to the position, as in the 2D kernel.  OU: the drift
+// mu - kappa x is evaluated at the current position x + s (s the block's
+// partial sum); without it the constant drift mu dt is added once per block.
+template <bool OU>
 __global__ void __launch_bounds__(kWalkBlock) walk3d_fwd_kernel(Walk3dArgs a, const float *__restrict__ x0_in,
                                                                float *__restrict__ xT, float *__restrict__ ckpt,
                                                                double *__restrict__ partials)
@@ -215,9 +221,10 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_fwd_kernel(Walk3dArgs a, co
         } else {
             walk3d_x0(keys, x);
         }
+        const bool want_ck = ckpt != nullptr && a.K != 0;  // every block must advance t
         uint32_t next_ck = 0, j = 0;
-        for (uint32_t t = 0; t < a.steps; ++t) {
-            if (ckpt && t == next_ck) {
+        for (uint32_t t = 0; t < a.steps;) {
+            if (want_ck && t == next_ck) {
                 float *dst = ckpt + ((size_t)j * a.n + i) * 3;
                 dst[0] = x[0];
                 dst[1] = x[1];
@@ -225,10 +232,21 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_fwd_kernel(Walk3dArgs a, co
                 ++j;
                 next_ck += a.K;
             }
-            float z[3];
-            walk3d_scaled_normals(keys, t + 1u, a.sig_sqdt, z);
+            uint32_t len = min(kSumBlock, a.steps - t);
+            if (want_ck) len = min(len, next_ck - t);
+            float sum[3] = {0.f, 0.f, 0.f};
+            for (uint32_t k = 0; k < len; ++k) {
+                float z[3];
+                walk3d_scaled_normals(keys, t + k + 1u, a.sig_sqdt, z);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], fmaf(-a.kappa_dt, x[q], z[q] + a.mu_dt[q]));
+                for (int q = 0; q < 3; ++q) {
+                    if (OU) sum[q] += fmaf(-a.kappa_dt, x[q] + sum[q], z[q] + a.mu_dt[q]);
+                    else sum[q] += z[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], OU ? sum[q] : fmaf((float)len, a.mu_dt[q], sum[q]));
+            t += len;
         }
         xT[3 * i] = x[0];
         xT[3 * i + 1] = x[1];
@@ -267,12 +285,20 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_bwd_kernel(Walk3dArgs a, co
 #pragma unroll
         for (int q = 0; q < 3; ++q) lam[q] = a.k_over_p * (double)xT[3 * i + q] * gl;
         if constexpr (!OU) {
+            // S = sum of z_t, in blocks of kSumBlock steps Kahan-added to S.
             float S[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
-            for (uint32_t tt = a.steps; tt > 0; --tt) {
-                float z[3];
-                walk3d_normals(keys, tt, z);   // z_{tt-1} uses counter tt
+            for (uint32_t tt = a.steps; tt > 0;) {
+                const uint32_t len = min(kSumBlock, tt);
+                float sum[3] = {0.f, 0.f, 0.f};
+                for (uint32_t k = 0; k < len; ++k) {
+                    float z[3];
+                    walk3d_normals(keys, tt - k, z);   // z_{t-1} uses counter t
 #pragma unroll
-                for (int q = 0; q < 3; ++q) kahan_add(S[q], c[q], z[q]);
+                    for (int q = 0; q < 3; ++q) sum[q] += z[q];
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) kahan_add(S[q], c[q], sum[q]);
+                tt -= len;
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -558,7 +584,8 @@ orand_status_t orand_walk3d_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
         if ((st = ctx_scratch(ctx, (size_t)grid * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
         partials = (double *)scr;
     }
-    walk3d_fwd_kernel<<<grid, kWalkBlock, 0, stream>>>(a, x0, xT, ckpt, partials);
+    if (p->kappa != 0.0f) walk3d_fwd_kernel<true><<<grid, kWalkBlock, 0, stream>>>(a, x0, xT, ckpt, partials);
+    else walk3d_fwd_kernel<false><<<grid, kWalkBlock, 0, stream>>>(a, x0, xT, ckpt, partials);
     if ((st = launch_status()) != ORAND_OK || !loss) return st;
     reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, a.k_over_p, nullptr, loss, 1);
     return launch_status();
