@@ -145,13 +145,34 @@ def test_tyche_words_are_b_after_each_mix(orc):
 _TF_ROT = [(10, 26), (11, 21), (13, 27), (23, 5), (6, 20), (17, 11), (25, 10), (18, 20)]
 
 
+def _skein_c240():
+    """Skein's key-schedule parity constant C240, derived as Skein does: the
+    AES-256 encryption, under the all-zero key, of the number 240 (a 16-byte
+    big-endian block); C240 is the last 8 bytes of the result.  AES comes
+    from the ``cryptography`` package, outside this project."""
+    from cryptography.hazmat.primitives.ciphers import Cipher, algorithms, modes
+
+    enc = Cipher(algorithms.AES(bytes(32)), modes.ECB()).encryptor()
+    ct = enc.update((240).to_bytes(16, "big")) + enc.finalize()
+    return int.from_bytes(ct[8:], "big")
+
+
+# Threefry's 32-bit parity word is the high half of C240.
+_TF_PARITY = _skein_c240() >> 32
+
+
+def test_threefry_parity_constant_is_skein_c240():
+    assert _skein_c240() == 0x1BD11BDAA9FC1A22
+    assert _TF_PARITY == 0x1BD11BDA
+
+
 def _rotr(x, r):
     return ((x >> r) | (x << (32 - r))) & M32
 
 
 def _threefry_inverse(out, key):
     """Inverse of Threefry4x32-20 (undo each injection and round in reverse)."""
-    ks = list(key) + [0x1BD11BDA ^ key[0] ^ key[1] ^ key[2] ^ key[3]]
+    ks = list(key) + [_TF_PARITY ^ key[0] ^ key[1] ^ key[2] ^ key[3]]
     x = list(out)
     for r in range(19, -1, -1):
         if r % 4 == 3:
