@@ -269,6 +269,56 @@ def stream_test_rows(torch, orand, W, rank, n_words=1 << 30):
     return rows, keep
 
 
+def stored_walk3d_baseline(torch, orand, W, reps=2, chunk=1 << 20):
+    """The fused walk with stored noise (one forward launch that also writes
+    z_t, one backward launch that reads it back), the other side of the
+    regeneration trade-off, over particle chunks of 48 GiB of noise."""
+    c3 = W.WALK3D
+    P3, T = c3["n_particles"], c3["steps"]
+    ctx = orand.default_context().handle
+    sh = torch.cuda.current_stream().cuda_stream
+    z = torch.empty((T, chunk, 3), dtype=torch.float32, device="cuda")
+    xT = torch.empty((chunk, 3), dtype=torch.float32, device="cuda")
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    dmu = torch.empty(3, dtype=torch.float64, device="cuda")
+    dsig = torch.empty((), dtype=torch.float64, device="cuda")
+    dx0 = torch.empty_like(xT)
+    times, fwd_ms = [], []
+    for r in range(reps + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        m = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        f_ms = 0.0
+        torch.cuda.synchronize()
+        a.record()
+        for c0 in range(0, P3, chunk):
+            prm = orand.walk3d_params(chunk, T, c3["dt"], c3["mu"], c3["sigma"], c3["k"], c3["seed"], 0,
+                                      p_first=c0, p_total=P3)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            orand.orand_walk3d_stored_fwd(ctx, prm, 0, xT.data_ptr(), z.data_ptr(), loss.data_ptr(), sh)
+            e1.record()
+            orand.orand_walk3d_stored_bwd(ctx, prm, xT.data_ptr(), z.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(),
+                                          dx0.data_ptr(), sh)
+            torch.cuda.synchronize()
+            f_ms += e0.elapsed_time(e1)
+        b.record()
+        torch.cuda.synchronize()
+        if r:
+            times.append(a.elapsed_time(b))
+            fwd_ms.append(f_ms)
+    del z
+    torch.cuda.empty_cache()
+    ms = statistics.mean(times)
+    z_bytes = P3 * T * 12
+    return {"ms": round(ms, 3), "fwd_ms": round(statistics.mean(fwd_ms), 3),
+            "particle_steps_per_s": P3 * T / (ms * 1e-3),
+            "pattern": "fused forward writing z (12 B per particle-step), fused backward reading it",
+            "noise_bytes": z_bytes, "hbm_needed_GiB": round(z_bytes / 2**30, 1),
+            "chunks": P3 // chunk}
+
+
 def ragged_serial_baseline(torch, orand, W, n_sub=2000, reps=2):
     """One bulk-fill launch per request (in order, one stream) vs the batcher,
     on the first n_sub requests of the list (the full list's serial Tyche
@@ -619,6 +669,11 @@ def main():
         if fused:
             plain["fused_speedup"] = round(plain["ms"] / fused["ms"], 3)
         baselines["walk3d/plain_noise_storing_fwd+bwd"] = plain
+        stored = stored_walk3d_baseline(torch, orand, W)
+        if fused:
+            stored["regenerating_ms"] = fused["ms"]
+            stored["regenerating_over_stored"] = round(fused["ms"] / stored["ms"], 3)
+        baselines["walk3d/fused_noise_storing_fwd+bwd"] = stored
         baselines["ragged/one_launch_per_request_first2000"] = ragged_serial_baseline(torch, orand, W)
         baselines["curand_philox4_32_10_2^28_values"] = curand_reference(torch)
         baselines["paper_brownian_dynamics_1e6x1e4"] = paper_brownian_benchmark(torch, orand)

@@ -243,6 +243,21 @@ orand_status_t orand_walk3d_plain_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, 
                                       const float *z_store, const double *grad_loss, double *dmu,
                                       double *dsigma, float *dx0, cudaStream_t stream);
 
+/* Fused noise-storing variant of the same walk (kappa must be 0): the
+ * other side of the adjoint's regeneration trade-off.  The forward is the
+ * fused, register-resident walk of orand_walk3d_fwd that also writes every
+ * standard normal z_t to z_store[t][i][3] (steps x n_particles x 3 floats,
+ * 12 bytes per particle-step) and no checkpoints; the backward reads z back
+ * from z_store instead of regenerating it.  Same outputs as
+ * orand_walk3d_fwd / orand_walk3d_bwd up to FP32 rounding order; z_store
+ * holds the same values the plain baseline stores.  Errors: as the plain
+ * baseline. */
+orand_status_t orand_walk3d_stored_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *xT,
+                                       float *z_store, double *loss, cudaStream_t stream);
+orand_status_t orand_walk3d_stored_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
+                                       const float *z_store, const double *grad_loss, double *dmu, double *dsigma,
+                                       float *dx0, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * Ragged batched generation.  Request i asks for `length` values of
  * `dtype` from the single stream (gen, key64 = seed, counter): exactly the

@@ -64,6 +64,8 @@ _SIGS = {
     "orand_walk3d_bwd_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_plain_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_walk3d_stored_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "orand_walk3d_stored_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_langevin2d_init": (_i32, [_vp, _vp, _vp]),
     "orand_langevin2d_step": (_i32, [_vp, _vp, _u32, _vp]),
     "orand_langevin2d_fused": (_i32, [_vp, _vp, _u32, _u32, _vp]),
@@ -421,6 +423,17 @@ def orand_walk3d_bwd_noalloc(params, xT_ptr, ckpt_ptr, grad_loss_ptr, dmu_ptr, d
 def orand_walk3d_plain_fwd(ctx, params, x0_ptr, x_ptr, z_ptr, loss_ptr, stream_handle):
     _check(_lib().orand_walk3d_plain_fwd(ctx, ctypes.byref(params), x0_ptr, x_ptr, z_ptr, loss_ptr,
                                          stream_handle), "orand_walk3d_plain_fwd")
+
+
+def orand_walk3d_stored_fwd(ctx, params, x0_ptr, xT_ptr, z_store_ptr, loss_ptr, stream_handle):
+    _check(_lib().orand_walk3d_stored_fwd(ctx, ctypes.byref(params), x0_ptr, xT_ptr, z_store_ptr, loss_ptr,
+                                          stream_handle), "orand_walk3d_stored_fwd")
+
+
+def orand_walk3d_stored_bwd(ctx, params, xT_ptr, z_store_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dx0_ptr,
+                            stream_handle):
+    _check(_lib().orand_walk3d_stored_bwd(ctx, ctypes.byref(params), xT_ptr, z_store_ptr, grad_loss_ptr, dmu_ptr,
+                                          dsigma_ptr, dx0_ptr, stream_handle), "orand_walk3d_stored_bwd")
 
 
 def orand_walk3d_plain_bwd(ctx, params, xT_ptr, z_ptr, grad_loss_ptr, dmu_ptr, dsigma_ptr, dx0_ptr,

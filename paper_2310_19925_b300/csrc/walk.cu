@@ -350,6 +350,89 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_bwd_kernel(Walk3dArgs a, co
     block_reduce_store<kRedWidth>(g, partials);
 }
 
+// ------------------------------------------- fused noise-storing baseline
+//
+// The other side of the regeneration trade-off: the same fused forward
+// (constant drift, block sums) also writes every standard normal z_t to
+// z_store[t][i][3], and the backward reads z back instead of regenerating
+// it.  This costs 12 bytes of HBM per particle-step (written once, read
+// once) in exchange for the backward's random-number work.
+
+__global__ void __launch_bounds__(kWalkBlock) stored_fwd_kernel(Walk3dArgs a, const float *__restrict__ x0_in,
+                                                               float *__restrict__ xT, float *__restrict__ z_store,
+                                                               double *__restrict__ partials)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    double loss[kRedWidth] = {};
+    if (i < a.n) {
+        const orand::PhiloxKeys keys(a.seed ^ (a.p_first + i));
+        float x[3], c[3] = {0.f, 0.f, 0.f};
+        if (x0_in) {
+            x[0] = x0_in[3 * i];
+            x[1] = x0_in[3 * i + 1];
+            x[2] = x0_in[3 * i + 2];
+        } else {
+            walk3d_x0(keys, x);
+        }
+        for (uint32_t t = 0; t < a.steps;) {
+            const uint32_t len = min(kSumBlock, a.steps - t);
+            float sum[3] = {0.f, 0.f, 0.f};
+            for (uint32_t k = 0; k < len; ++k) {
+                float z[3];
+                walk3d_normals(keys, t + k + 1u, z);
+                float *dst = z_store + ((size_t)(t + k) * a.n + i) * 3;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    dst[q] = z[q];
+                    sum[q] = fmaf(a.sig_sqdt, z[q], sum[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], fmaf((float)len, a.mu_dt[q], sum[q]));
+            t += len;
+        }
+        xT[3 * i] = x[0];
+        xT[3 * i + 1] = x[1];
+        xT[3 * i + 2] = x[2];
+        loss[0] = 0.5 * ((double)x[0] * x[0] + (double)x[1] * x[1] + (double)x[2] * x[2]);
+    }
+    if (partials) block_reduce_store<kRedWidth>(loss, partials);
+}
+
+__global__ void __launch_bounds__(kWalkBlock) stored_bwd_kernel(Walk3dArgs a, const float *__restrict__ xT,
+                                                               const float *__restrict__ z_store,
+                                                               const double *__restrict__ grad_loss,
+                                                               float *__restrict__ dx0, double *__restrict__ partials)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * kWalkBlock + threadIdx.x;
+    double g[kRedWidth] = {};
+    if (i < a.n) {
+        const double gl = grad_loss ? *grad_loss : 1.0;
+        float S[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+        for (uint32_t t = 0; t < a.steps;) {
+            const uint32_t len = min(kSumBlock, a.steps - t);
+            float sum[3] = {0.f, 0.f, 0.f};
+#pragma unroll 8
+            for (uint32_t k = 0; k < len; ++k) {
+                const float *src = z_store + ((size_t)(t + k) * a.n + i) * 3;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) sum[q] += __ldg(src + q);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) kahan_add(S[q], c[q], sum[q]);
+            t += len;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const double lam = a.k_over_p * (double)xT[3 * i + q] * gl;
+            g[q] = lam * a.t_dt;
+            g[3] += lam * a.sqdt * (double)S[q];
+            if (dx0) dx0[3 * i + q] = (float)lam;
+        }
+    }
+    block_reduce_store<kRedWidth>(g, partials);
+}
+
 // ------------------------------------------- plain noise-storing baseline
 
 __global__ void __launch_bounds__(kWalkBlock) plain_init_kernel(Walk3dArgs a, const float *__restrict__ x0_in,
@@ -661,6 +744,61 @@ orand_status_t orand_walk3d_plain_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, 
     for (uint32_t tt = a.steps; tt > 0; --tt)
         plain_bwd_step_kernel<<<g3, kWalkBlock, 0, stream>>>(n3, z_store + (size_t)(tt - 1) * n3, S);
     plain_bwd_final_kernel<<<grid, kWalkBlock, 0, stream>>>(a, xT, S, grad_loss, dx0, partials);
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
+    return launch_status();
+}
+
+orand_status_t orand_walk3d_stored_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *xT,
+                                       float *z_store, double *loss, cudaStream_t stream)
+{
+    Walk3dArgs a;
+    orand_status_t st = walk3d_args(p, &a);
+    if (st != ORAND_OK) return st;
+    if (p->kappa != 0.0f) return ORAND_ERR_INVALID_ARG;  // the baseline is the constant-drift walk
+    if ((st = ctx_check(ctx)) != ORAND_OK) return st;
+    if (a.n == 0) {
+        if (loss) return cuda_status(cudaMemsetAsync(loss, 0, sizeof(double), stream));
+        return ORAND_OK;
+    }
+    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
+    if (a.steps && (st = check_ptr(z_store, 4)) != ORAND_OK) return st;
+    if (x0 && ((uintptr_t)x0 % 4)) return ORAND_ERR_ALIGNMENT;
+    if (loss && ((uintptr_t)loss % 8)) return ORAND_ERR_ALIGNMENT;
+    const unsigned grid = walk_grid(a.n);
+    double *partials = nullptr;
+    if (loss) {
+        void *scr = nullptr;
+        if ((st = ctx_scratch(ctx, (size_t)grid * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
+        partials = (double *)scr;
+    }
+    stored_fwd_kernel<<<grid, kWalkBlock, 0, stream>>>(a, x0, xT, z_store, partials);
+    if ((st = launch_status()) != ORAND_OK || !loss) return st;
+    reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, a.k_over_p, nullptr, loss, 1);
+    return launch_status();
+}
+
+orand_status_t orand_walk3d_stored_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *xT,
+                                       const float *z_store, const double *grad_loss, double *dmu, double *dsigma,
+                                       float *dx0, cudaStream_t stream)
+{
+    Walk3dArgs a;
+    orand_status_t st = walk3d_args(p, &a);
+    if (st != ORAND_OK) return st;
+    if (p->kappa != 0.0f) return ORAND_ERR_INVALID_ARG;
+    if ((st = ctx_check(ctx)) != ORAND_OK) return st;
+    if ((st = check_ptr(dmu, 8)) != ORAND_OK || (st = check_ptr(dsigma, 8)) != ORAND_OK) return st;
+    if (a.n == 0) return bwd_zero(dmu, dsigma, nullptr, stream);
+    if ((st = check_ptr(xT, 4)) != ORAND_OK) return st;
+    if (a.steps && (st = check_ptr(z_store, 4)) != ORAND_OK) return st;
+    if (dx0 && ((uintptr_t)dx0 % 4)) return ORAND_ERR_ALIGNMENT;
+    if (grad_loss && ((uintptr_t)grad_loss % 8)) return ORAND_ERR_ALIGNMENT;
+    const unsigned grid = walk_grid(a.n);
+    void *scr = nullptr;
+    if ((st = ctx_scratch(ctx, (size_t)grid * kRedWidth * sizeof(double), &scr)) != ORAND_OK) return st;
+    double *partials = (double *)scr;
+    stored_bwd_kernel<<<grid, kWalkBlock, 0, stream>>>(a, xT, z_store, grad_loss, dx0, partials);
+    if ((st = launch_status()) != ORAND_OK) return st;
     reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
     reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
     return launch_status();

@@ -89,6 +89,9 @@ def test_walk_arguments_rejected_on_host(lib):
     assert lib.orand_walk3d_fwd(None, None, None, 16, None, None, None) == -1
     bad = orand.walk3d_params(10, 5, sigma=-0.5)
     assert lib.orand_walk3d_bwd(None, ctypes.byref(bad), 16, None, None, 16, 16, None, None, None) == -1
+    ou = orand.walk3d_params(10, 5, kappa=1.0)
+    assert lib.orand_walk3d_stored_fwd(None, ctypes.byref(ou), None, 16, 16, None, None) == -1   # kappa != 0
+    assert lib.orand_walk3d_stored_bwd(None, ctypes.byref(ou), 16, 16, None, 16, 16, None, None) == -1
     big = orand.walk3d_params(2**40, 5)
     assert lib.orand_walk3d_init(ctypes.byref(big), 16, None) == -2                      # grid too large
     steps_max = orand.walk3d_params(1, 2**32 - 1)

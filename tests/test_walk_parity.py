@@ -308,3 +308,75 @@ def test_walk3d_ou_autograd_and_central_differences(torch_cuda, orc):
         lm = BW.apply(mu, sigma, x0, steps, 1e-3, 2.0, 0, K, kappa - h).item()
     kp, km = _f32(_f32(2.5) + h), _f32(_f32(2.5) - h)
     assert (lp - lm) / (kp - km) == pytest.approx(kappa.grad.item(), rel=GRAD_TOL)
+
+
+# ------------------------------------------- fused noise-storing variant ----
+
+def _stored_run(torch, p, n, steps):
+    ctx = orand.default_context().handle
+    sh = torch.cuda.current_stream().cuda_stream
+    xT = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    z = torch.empty((steps, n, 3), dtype=torch.float32, device="cuda")
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    orand.orand_walk3d_stored_fwd(ctx, p, 0, xT.data_ptr(), z.data_ptr(), loss.data_ptr(), sh)
+    dmu = torch.empty(3, dtype=torch.float64, device="cuda")
+    dsig = torch.empty((), dtype=torch.float64, device="cuda")
+    dx0 = torch.empty_like(xT)
+    g = torch.tensor(0.5, dtype=torch.float64, device="cuda")
+    orand.orand_walk3d_stored_bwd(ctx, p, xT.data_ptr(), z.data_ptr(), g.data_ptr(), dmu.data_ptr(),
+                                  dsig.data_ptr(), dx0.data_ptr(), sh)
+    torch.cuda.synchronize()
+    return xT, z, loss, dmu, dsig, dx0
+
+
+@pytest.mark.parametrize("n,steps", [(4096 + 33, 100), (1, 17), (300, 0)])
+def test_walk3d_stored_matches_regenerating_and_plain(torch_cuda, orc, n, steps):
+    """Stored noise equals the plain baseline's bit for bit; positions,
+    loss and gradients equal the regenerating walk's and the oracle's."""
+    torch = torch_cuda
+    p = _p(n, steps, K=16, p_first=9, p_total=2 * n)
+    xT, z, loss, dmu, dsig, dx0 = _stored_run(torch, p, n, steps)
+    rxT, _, rloss = orand.walk3d_forward(p, want_ckpt=False)
+    g = torch.tensor(0.5, dtype=torch.float64, device="cuda")
+    rdmu, rdsig, rdx0 = orand.walk3d_backward(p, rxT, g)
+    torch.cuda.synchronize()
+    oxT, _ = orc.walk3d_forward(0, n, steps, 16, _f32(1e-3), MU, 0.5, p_first=9)
+    pos_close(to_numpy(xT), oxT)
+    assert loss.item() == pytest.approx(rloss.item(), rel=GRAD_TOL)
+    assert np.allclose(to_numpy(dmu), to_numpy(rdmu), rtol=GRAD_TOL)
+    assert dsig.item() == pytest.approx(rdsig.item(), rel=GRAD_TOL, abs=1e-12)
+    np.testing.assert_allclose(to_numpy(dx0), to_numpy(rdx0), rtol=GRAD_TOL, atol=1e-12)
+    if steps:
+        ctx = orand.default_context().handle
+        x = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        zp = torch.empty((steps, n, 3), dtype=torch.float32, device="cuda")
+        orand.orand_walk3d_plain_fwd(ctx, p, 0, x.data_ptr(), zp.data_ptr(), 0, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.equal(z, zp)
+
+
+def test_walk3d_stored_full_steps_subset(torch_cuda, orc):
+    """4096 steps on a 2^18-particle range of the 2^22-particle workload
+    (12.9 GB of stored noise): gradients against the regenerating adjoint,
+    and a particle-range subset against the FP64 oracle adjoint."""
+    torch = torch_cuda
+    c = W.WALK3D
+    n, T = 1 << 18, c["steps"]
+    p = orand.walk3d_params(n, T, c["dt"], c["mu"], c["sigma"], c["k"], c["seed"], 0, p_first=777, p_total=c["n_particles"])
+    xT, z, loss, dmu, dsig, dx0 = _stored_run(torch, p, n, T)
+    del z
+    rxT, _, _ = orand.walk3d_forward(p, want_ckpt=False)
+    g = torch.tensor(0.5, dtype=torch.float64, device="cuda")
+    rdmu, rdsig, _ = orand.walk3d_backward(p, rxT, g)
+    torch.cuda.synchronize()
+    assert torch.allclose(xT, rxT, rtol=POS_TOL, atol=POS_TOL)
+    assert np.allclose(to_numpy(dmu), to_numpy(rdmu), rtol=GRAD_TOL)
+    assert dsig.item() == pytest.approx(rdsig.item(), rel=GRAD_TOL)
+    sub = orand.walk3d_params(512, T, c["dt"], c["mu"], c["sigma"], c["k"], c["seed"], 0, p_first=777,
+                              p_total=c["n_particles"])
+    sxT, _, _, sdmu, sdsig, _ = _stored_run(torch, sub, 512, T)
+    dt32 = _f32(c["dt"])
+    oxT, _ = orc.walk3d_forward(c["seed"], 512, T, 64, dt32, c["mu"], c["sigma"], p_first=777, threads=8)
+    odmu, odsig, _ = orc.walk3d_adjoint(c["seed"], 512, T, dt32, oxT, c["k"], c["n_particles"], p_first=777, threads=8)
+    assert np.allclose(to_numpy(sdmu), 0.5 * odmu, rtol=GRAD_TOL)
+    assert sdsig.item() == pytest.approx(0.5 * odsig, rel=GRAD_TOL)
