@@ -269,6 +269,41 @@ def stream_test_rows(torch, orand, W, rank, n_words=1 << 30):
     return rows, keep
 
 
+def curand_walk2d_baseline(torch, orand, W, reps=1):
+    """cuRAND's Philox device API on the 2D walk at full size: the paper's
+    Fig. 2 pattern (states and positions in HBM, one launch per step) and a
+    fused form with the state in registers."""
+    c2 = W.WALK2D
+    P2, T = c2["n_particles"], c2["steps"]
+    sh = torch.cuda.current_stream().cuda_stream
+    prm = orand.walk2d_params(P2, T, c2["dt"], c2["D"], c2["seed"])
+    states = torch.empty(P2 * orand.orand_walk2d_curand_state_bytes(), dtype=torch.uint8, device="cuda")
+    pos = torch.empty((P2, 2), dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        ts = []
+        for r in range(reps + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b))
+        return statistics.mean(ts)
+
+    per_step = timed(lambda: (orand.orand_walk2d_curand_setup(prm, states.data_ptr(), pos.data_ptr(), 1984, sh),
+                              orand.orand_walk2d_curand_run(prm, states.data_ptr(), pos.data_ptr(), sh)))
+    fused = timed(lambda: orand.orand_walk2d_curand_fused(prm, pos.data_ptr(), 1984, sh))
+    del states
+    torch.cuda.empty_cache()
+    return {"per_step_ms": round(per_step, 3), "fused_ms": round(fused, 3),
+            "state_bytes": orand.orand_walk2d_curand_state_bytes(),
+            "pattern": "cuRAND Philox: Fig. 2 (state in HBM, one launch per step) and fused (state in registers)"}
+
+
 def stored_walk3d_baseline(torch, orand, W, reps=2, chunk=1 << 20):
     """The fused walk with stored noise (one forward launch that also writes
     z_t, one backward launch that reads it back), the other side of the
@@ -676,6 +711,13 @@ def main():
         baselines["walk3d/fused_noise_storing_fwd+bwd"] = stored
         baselines["ragged/one_launch_per_request_first2000"] = ragged_serial_baseline(torch, orand, W)
         baselines["curand_philox4_32_10_2^28_values"] = curand_reference(torch)
+        cw = curand_walk2d_baseline(torch, orand, W)
+        w2 = row_table.get("walk2d/fused")
+        if w2:
+            cw["orand_fused_ms"] = w2["ms"]
+            cw["curand_fused_over_orand"] = round(cw["fused_ms"] / w2["ms"], 3)
+            cw["curand_per_step_over_orand"] = round(cw["per_step_ms"] / w2["ms"], 3)
+        baselines["walk2d/curand_2^24x10^4"] = cw
         baselines["paper_brownian_dynamics_1e6x1e4"] = paper_brownian_benchmark(torch, orand)
         from paper_2310_19925_b300 import host_bench
 

@@ -145,6 +145,38 @@ typedef struct orand_walk2d_t {
 } orand_walk2d_t;
 orand_status_t orand_brownian_walk(const orand_walk2d_t *p, float *pos_out, cudaStream_t stream);
 
+/* cuRAND comparison for the same walk (the paper's comparison system,
+ * Fig. 2), with cuRAND's Philox device generator: particle i's state comes
+ * from curand_init(curand_seed, p_first + i, 0), its start position from
+ * two curand_uniform draws, and each step adds s * curand_normal2.  These
+ * are different streams from orand_brownian_walk's; only the cost model is
+ * compared.  p->seed is not used.
+ *   orand_walk2d_curand_setup: initialise n_particles states (caller-owned,
+ *     orand_walk2d_curand_state_bytes() each, 16-byte aligned) and write the
+ *     start positions to pos_out.
+ *   orand_walk2d_curand_run: Fig. 2's pattern, p->steps launches, each
+ *     loading every state and position from HBM and storing them back.
+ *   orand_walk2d_curand_fused: one launch, the state in registers for all
+ *     steps, the same block-compensated sums as orand_brownian_walk.
+ * pos: 2 * n_particles floats, 8-byte aligned.  Errors: as
+ * orand_brownian_walk, plus INVALID_ARG / ALIGNMENT for the states. */
+size_t orand_walk2d_curand_state_bytes(void);
+orand_status_t orand_walk2d_curand_setup(const orand_walk2d_t *p, void *states, float *pos_out, uint64_t curand_seed,
+                                         cudaStream_t stream);
+orand_status_t orand_walk2d_curand_run(const orand_walk2d_t *p, void *states, float *pos, cudaStream_t stream);
+orand_status_t orand_walk2d_curand_fused(const orand_walk2d_t *p, float *pos_out, uint64_t curand_seed,
+                                         cudaStream_t stream);
+
+/* The walks' Box-Muller map (the normals every walk kernel draws): for
+ * each pair i, out[2i] = r cos(2 pi u2), out[2i+1] = r sin(2 pi u2) with
+ * u1 = ((words[2i] >> 8) + 1) 2^-24 and u2 = (words[2i+1] >> 8) 2^-24, from
+ * the SFU's estimates: r within 5.8e-7 relative of sqrt(-2 ln u1), cos and
+ * sin within 3.4e-7 absolute (measured over every input).  The fills use
+ * the exact-to-3-ulp map (orand_map_words with ORAND_F32_NORMAL).
+ * words: 2 n_pairs u32, out: 2 n_pairs floats, device memory, 4-byte aligned.
+ * Errors: INVALID_ARG, OVERFLOW, ALIGNMENT, CUDA. */
+orand_status_t orand_walk_normals(const uint32_t *words, uint64_t n_pairs, float *out, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * Differentiable 3D Brownian walk with drift mu - kappa x (kappa = 0: the
  * constant-drift walk; kappa > 0: Ornstein-Uhlenbeck).

@@ -28,7 +28,9 @@
  * one high (Fig. 3), ((hi:lo) >> 11) * 2^-53, built with integer ops only;
  * Box-Muller with u1 = ((w0>>8)+1) * 2^-24, u2 = (w1>>8) * 2^-24,
  * r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2), using the library's own
- * reduced-range log and sincospi (within 3 ulp of the FP64 values).
+ * reduced-range log and sincospi (within 3 ulp of the FP64 values).  The
+ * walk kernels use a cheaper map of the same form (bm_radius_walk,
+ * bm_cos_sin_walk), accurate to about 1e-6.
  */
 #pragma once
 
@@ -410,6 +412,76 @@ __device__ __forceinline__ float box_muller_cos_f32(uint32_t w0, uint32_t w1)
     float c, s;
     bm_cos_sin(w1, &c, &s);
     return bm_radius(w0) * c;
+}
+
+/* ---------------------------------------------- the walks' Box-Muller map
+ *
+ * The walk kernels only need their normals to about 1e-6 (positions are
+ * checked to 1e-5 after 10^4 steps), so they use a cheaper map from the
+ * same words, built on the SFU's estimates (lg2.approx, rsqrt.approx,
+ * sin.approx, cos.approx, used as PTX instructions).  Measured over every
+ * input: the radius is within 5.8e-7 relative of sqrt(-2 ln u1), and the
+ * cosine and sine within 3.4e-7 absolute of cos and sin(2 pi u2).  The fills
+ * keep the map above (within 3 ulp). */
+
+__device__ __forceinline__ float sfu_lg2(float x) { float y; asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_rsqrt(float x) { float y; asm("rsqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_sin(float x) { float y; asm("sin.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_cos(float x) { float y; asm("cos.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+
+/* sqrt(-2 ln u1), u1 = ((w0 >> 8) + 1) 2^-24.  With v = 1 - u1 (exact):
+ * for v < 1/16, -2 ln(1 - v) = 2 v (1 + v/2 + v^2/3 + v^3/4 + v^4/5 + v^5/6)
+ * (the first omitted term is below 1e-8 relative); elsewhere the SFU's
+ * log2 estimate, whose absolute error (about 7e-8) would be a large
+ * relative error next to u1 = 1.  Both are evaluated and one is selected,
+ * so the lanes of a warp never diverge. */
+__device__ __forceinline__ float bm_radius_walk(uint32_t w0)
+{
+    const float u1 = __uint2float_rn((w0 >> 8) + 1u) * 0x1p-24f;
+    const float v = 1.0f - u1;
+    float p = fmaf(v, 1.0f / 6.0f, 0.2f);
+    p = fmaf(p, v, 0.25f);
+    p = fmaf(p, v, 1.0f / 3.0f);
+    p = fmaf(p, v, 0.5f);
+    p = fmaf(p, v, 1.0f);
+    const float x_series = 2.0f * v * p;
+    const float x_log = -1.3862943611198906f * sfu_lg2(u1);   /* -2 ln 2 log2(u1) */
+    const float x = v < 0.0625f ? x_series : x_log;
+    return x > 0.0f ? x * sfu_rsqrt(x) : 0.0f;
+}
+
+/* (cos, sin)(2 pi u2), u2 = (w1 >> 8) 2^-24, by the exact quadrant
+ * reduction of bm_cos_sin (q = round(4 u2), r = 2 u2 - q/2 in [-1/4, 1/4])
+ * and the SFU's estimates at pi r in [-pi/4, pi/4].  The reduction matters
+ * for more than range: the cosine estimate has a small mean error, and
+ * through the quadrant swap and signs it enters c as +, -, -, + over the
+ * four quadrants, so the walk's sum of normals carries no drift from it
+ * (a walk of 10^4 steps would otherwise move by about 1e-5). */
+__device__ __forceinline__ void bm_cos_sin_walk(uint32_t w1, float *c, float *s)
+{
+    const uint32_t m = w1 >> 8;
+    const uint32_t q = (m + (1u << 21)) >> 22;
+    const float th = (float)(int)(m - (q << 22)) * (0x1p-23f * 3.14159265358979324f);
+    const float sn = sfu_sin(th), cs = sfu_cos(th);
+    const bool swap = q & 1u;
+    const uint32_t a = __float_as_uint(swap ? cs : sn), b = __float_as_uint(swap ? sn : cs);
+    *s = __uint_as_float(a ^ ((q & 2u) << 30));                /* negate sin for q = 2, 3 */
+    *c = __uint_as_float(b ^ (((q + 1u) & 2u) << 30));         /* negate cos for q = 1, 2 */
+}
+
+__device__ __forceinline__ float2 box_muller_walk_f32(uint32_t w0, uint32_t w1)
+{
+    const float r = bm_radius_walk(w0);
+    float c, s;
+    bm_cos_sin_walk(w1, &c, &s);
+    return make_float2(r * c, r * s);
+}
+
+__device__ __forceinline__ float box_muller_cos_walk_f32(uint32_t w0, uint32_t w1)
+{
+    float c, s;
+    bm_cos_sin_walk(w1, &c, &s);
+    return bm_radius_walk(w0) * c;
 }
 
 /* ------------------------------------------------ engine-style generators */

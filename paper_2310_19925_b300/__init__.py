@@ -58,6 +58,11 @@ _SIGS = {
     "orand_ctx_create": (_i32, [ctypes.POINTER(_vp)]),
     "orand_ctx_destroy": (_i32, [_vp]),
     "orand_brownian_walk": (_i32, [_vp, _vp, _vp]),
+    "orand_walk_normals": (_i32, [_vp, _u64, _vp, _vp]),
+    "orand_walk2d_curand_state_bytes": (_sz, []),
+    "orand_walk2d_curand_setup": (_i32, [_vp, _vp, _vp, _u64, _vp]),
+    "orand_walk2d_curand_run": (_i32, [_vp, _vp, _vp, _vp]),
+    "orand_walk2d_curand_fused": (_i32, [_vp, _vp, _u64, _vp]),
     "orand_walk3d_init": (_i32, [_vp, _vp, _vp]),
     "orand_walk3d_fwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "orand_walk3d_bwd": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -374,6 +379,36 @@ def walk2d_params(n_particles, steps, dt=1e-3, D=1.0, seed=0, p_first=0) -> Walk
 
 def orand_brownian_walk(params: Walk2DParams, pos_out_ptr, stream_handle):
     _check(_lib().orand_brownian_walk(ctypes.byref(params), pos_out_ptr, stream_handle), "orand_brownian_walk")
+
+
+def orand_walk2d_curand_state_bytes():
+    return int(_lib().orand_walk2d_curand_state_bytes())
+
+
+def orand_walk2d_curand_setup(params, states_ptr, pos_ptr, curand_seed, stream_handle):
+    _check(_lib().orand_walk2d_curand_setup(ctypes.byref(params), states_ptr, pos_ptr, curand_seed & (2**64 - 1),
+                                            stream_handle), "orand_walk2d_curand_setup")
+
+
+def orand_walk2d_curand_run(params, states_ptr, pos_ptr, stream_handle):
+    _check(_lib().orand_walk2d_curand_run(ctypes.byref(params), states_ptr, pos_ptr, stream_handle),
+           "orand_walk2d_curand_run")
+
+
+def orand_walk2d_curand_fused(params, pos_ptr, curand_seed, stream_handle):
+    _check(_lib().orand_walk2d_curand_fused(ctypes.byref(params), pos_ptr, curand_seed & (2**64 - 1),
+                                            stream_handle), "orand_walk2d_curand_fused")
+
+
+def walk_normals(words, stream=None):
+    """The walks' Box-Muller map on a CUDA tensor of 2n u32 words (int32 bits): 2n floats."""
+    import torch
+
+    w = words.contiguous()
+    out = torch.empty(w.numel(), dtype=torch.float32, device="cuda")
+    _check(_lib().orand_walk_normals(_ptr(w) if w.numel() else 0, w.numel() // 2, _ptr(out) if w.numel() else 0,
+                                     _stream_handle(stream)), "orand_walk_normals")
+    return out
 
 
 def brownian_walk(n_particles, steps, dt=1e-3, D=1.0, seed=0, p_first=0, out=None, stream=None):

@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(kWalk2dBlock) walk2d_kernel(uint64_t n, uint64
             for (int j = 0; j < kWalk2dPerThread; ++j) {
                 const uint4 w = L[j].keys.block(0u, t);
                 // s * (r cos, r sin) with the step scale folded into the radius.
-                const float rs = s * orand::bm_radius(w.x);
+                const float rs = s * orand::bm_radius_walk(w.x);
                 float c, sn;
-                orand::bm_cos_sin(w.y, &c, &sn);
+                orand::bm_cos_sin_walk(w.y, &c, &sn);
                 sx[j] = fmaf(rs, c, sx[j]);
                 sy[j] = fmaf(rs, sn, sy[j]);
             }
@@ -158,10 +158,10 @@ struct Walk3dArgs {
 __device__ __forceinline__ void walk3d_normals(const orand::PhiloxKeys &keys, uint32_t t_counter, float z[3])
 {
     const uint4 w = keys.block(0u, t_counter);
-    const float2 a = orand::box_muller_f32(w.x, w.y);
+    const float2 a = orand::box_muller_walk_f32(w.x, w.y);
     z[0] = a.x;
     z[1] = a.y;
-    z[2] = orand::box_muller_cos_f32(w.z, w.w);
+    z[2] = orand::box_muller_cos_walk_f32(w.z, w.w);
 }
 
 // sigma sqrt(dt) * (z0, z1, z2) with the scale folded into the two radii.
@@ -169,11 +169,11 @@ __device__ __forceinline__ void walk3d_scaled_normals(const orand::PhiloxKeys &k
                                                       float scale, float z[3])
 {
     const uint4 w = keys.block(0u, t_counter);
-    const float ra = scale * orand::bm_radius(w.x);
-    const float rb = scale * orand::bm_radius(w.z);
+    const float ra = scale * orand::bm_radius_walk(w.x);
+    const float rb = scale * orand::bm_radius_walk(w.z);
     float ca, sa, cb, sb;
-    orand::bm_cos_sin(w.y, &ca, &sa);
-    orand::bm_cos_sin(w.w, &cb, &sb);
+    orand::bm_cos_sin_walk(w.y, &ca, &sa);
+    orand::bm_cos_sin_walk(w.w, &cb, &sb);
     z[0] = ra * ca;
     z[1] = ra * sa;
     z[2] = rb * cb;
@@ -350,6 +350,18 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_bwd_kernel(Walk3dArgs a, co
     block_reduce_store<kRedWidth>(g, partials);
 }
 
+// The walks' Box-Muller map on word pairs, for inspection and testing.
+__global__ void __launch_bounds__(256) walk_normals_kernel(const uint32_t *__restrict__ words, uint64_t n_pairs,
+                                                          float *__restrict__ out)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pairs;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const float2 z = orand::box_muller_walk_f32(words[2 * i], words[2 * i + 1]);
+        out[2 * i] = z.x;
+        out[2 * i + 1] = z.y;
+    }
+}
+
 // ------------------------------------------- fused noise-storing baseline
 //
 // The other side of the regeneration trade-off: the same fused forward
@@ -460,8 +472,8 @@ __global__ void __launch_bounds__(kWalkBlock) plain_step_kernel(Walk3dArgs a, ui
     if (i >= a.n) return;
     const uint64_t key64 = a.seed ^ (a.p_first + i);
     const uint4 w = orand::philox_block(key64, t + 1u, 0u);
-    const float2 p = orand::box_muller_f32(w.x, w.y);
-    const float z[3] = {p.x, p.y, orand::box_muller_cos_f32(w.z, w.w)};
+    const float2 p = orand::box_muller_walk_f32(w.x, w.y);
+    const float z[3] = {p.x, p.y, orand::box_muller_cos_walk_f32(w.z, w.w)};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         z_t[3 * i + q] = z[q];
@@ -801,6 +813,18 @@ orand_status_t orand_walk3d_stored_bwd(orand_ctx_t ctx, const orand_walk3d_t *p,
     if ((st = launch_status()) != ORAND_OK) return st;
     reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials, grid, 1.0, nullptr, dmu, 3);
     reduce_partials_kernel<kRedWidth><<<1, 256, 0, stream>>>(partials + 3, grid, 1.0, nullptr, dsigma, 1);
+    return launch_status();
+}
+
+orand_status_t orand_walk_normals(const uint32_t *words, uint64_t n_pairs, float *out, cudaStream_t stream)
+{
+    if (n_pairs == 0) return ORAND_OK;
+    if (n_pairs > (UINT64_MAX >> 3)) return ORAND_ERR_OVERFLOW;
+    orand_status_t st;
+    if ((st = check_ptr(words, 4)) != ORAND_OK || (st = check_ptr(out, 4)) != ORAND_OK) return st;
+    DeviceInfo info;
+    if ((st = current_device(&info)) != ORAND_OK) return st;
+    walk_normals_kernel<<<grid_for(n_pairs, 256, info.sm_count, 8), 256, 0, stream>>>(words, n_pairs, out);
     return launch_status();
 }
 

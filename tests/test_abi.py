@@ -84,6 +84,11 @@ def test_walk_arguments_rejected_on_host(lib):
     assert lib.orand_brownian_walk(ctypes.byref(W2(4, 10)), 4, None) == -3              # not 8-byte aligned
     assert lib.orand_brownian_walk(ctypes.byref(W2(8, 10, p_first=2**64 - 4)), 8, None) == -2
     assert lib.orand_brownian_walk(ctypes.byref(W2(8, 2**32 - 1)), 8, None) == -2        # counter 2^32 - 1 limit
+    assert lib.orand_walk2d_curand_state_bytes() >= 48
+    assert lib.orand_walk2d_curand_setup(ctypes.byref(W2(4, 10)), None, 8, 0, None) == -1   # NULL states
+    assert lib.orand_walk2d_curand_setup(ctypes.byref(W2(4, 10)), 8, 8, 0, None) == -3      # misaligned states
+    assert lib.orand_walk2d_curand_run(ctypes.byref(W2(4, 10)), 16, 4, None) == -3          # misaligned pos
+    assert lib.orand_walk2d_curand_fused(ctypes.byref(W2(4, 10, dt=-1.0)), 8, 0, None) == -1
     p3 = orand.walk3d_params(10, 5)
     assert lib.orand_walk3d_fwd(None, ctypes.byref(p3), None, 16, None, None, None) == -1  # no context
     assert lib.orand_walk3d_fwd(None, None, None, 16, None, None, None) == -1

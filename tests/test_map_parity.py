@@ -101,3 +101,60 @@ def test_map_words_odd_counts_match_fill(torch_cuda, orc):
                 assert ulp_distance_f32(got, ref).max() <= 4
             else:
                 assert np.array_equal(got.astype(ref.dtype), ref)
+
+
+# ------------------------------------------------ the walks' normal map ----
+
+def walk_normals(torch, w0, w1):
+    words = np.empty(2 * len(w0), np.uint32)
+    words[0::2], words[1::2] = w0, w1
+    z = orand.walk_normals(torch.from_numpy(words.view(np.int32)).cuda())
+    torch.cuda.synchronize()
+    return to_numpy(z).reshape(-1, 2).astype(np.float64)
+
+
+def test_walk_map_radius_all_u1(torch_cuda, orc):
+    """Every u1 at u2 = 1/4 (cosine 0, sine 1): z1 is the radius, within
+    1e-6 relative of the FP64 value (measured 5.8e-7), and finite, non-negative
+    up to the cosine term, everywhere including u1 = 1."""
+    k = np.arange(1 << 24, dtype=np.uint32)
+    w0 = k << 8
+    w1 = np.full(k.size, 1 << 30, np.uint32)                     # u2 = 1/4
+    z = walk_normals(torch_cuda, w0, w1)
+    ref = orc.box_muller_array(w0, w1)
+    assert np.all(np.isfinite(z))
+    err = np.abs(z[:, 1] - ref[:, 1])
+    assert np.all(err <= 1e-6 * ref[:, 1] + 1e-30), "radius rel err %.3g at k=%d" % (
+        (err / np.maximum(ref[:, 1], 1e-30)).max(), int(k[err.argmax()]))
+    assert np.all(np.abs(z[:, 0]) <= 5e-7 * np.maximum(ref[:, 1], 1.0))   # r cos(pi/2) ~ 0
+    assert z[-1, 1] == 0.0                                       # u1 = 1 gives r = 0
+
+
+def test_walk_map_trig_all_u2(torch_cuda, orc):
+    """Every u2 at r = sqrt(2 ln 2): cos and sin within 4e-7 absolute of the
+    FP64 values times the radius, plus the radius error.  And no mean error:
+    a walk of T steps of size s drifts by T s E[r] times the mean error of
+    the cosine or sine, so it is held below 2e-10 (about 1e-7 over the 10^4
+    steps of the 2D workload)."""
+    m = np.arange(1 << 24, dtype=np.uint32)
+    w1 = m << 8
+    w0 = np.full(m.size, 0x7FFFFF00, np.uint32)                  # u1 = 1/2
+    z = walk_normals(torch_cuda, w0, w1)
+    ref = orc.box_muller_array(w0, w1)
+    r = np.sqrt(2 * np.log(2))
+    bound = 4e-7 * r + 1e-6 * np.abs(ref)
+    assert np.all(np.abs(z - ref) <= bound)
+    bias = (z - ref).mean(axis=0) / r
+    assert np.all(np.abs(bias) < 2e-10), bias
+
+
+def test_walk_map_random_pairs_and_moments(torch_cuda, orc):
+    rng = np.random.default_rng(3)
+    w = rng.integers(0, 2**32, size=(1 << 22, 2), dtype=np.uint64).astype(np.uint32)
+    z = walk_normals(torch_cuda, w[:, 0], w[:, 1])
+    ref = orc.box_muller_array(w[:, 0], w[:, 1])
+    rr = np.sqrt(ref[:, 0] ** 2 + ref[:, 1] ** 2)
+    assert np.all(np.abs(z - ref) <= (1e-6 + 4e-7) * rr[:, None] + 1e-12)
+    zz = z.ravel()
+    n = zz.size
+    assert abs(zz.mean()) < 5 / np.sqrt(n) and abs(zz.var() - 1) < 5 * np.sqrt(2 / n)

@@ -115,7 +115,9 @@ def test_walk3d_adjoint_small(torch_cuda, orc, n, steps):
     odmu, odsig, odx0 = orc.walk3d_adjoint(0, n, steps, _f32(1e-3), oxT, 2.0, 5 * n, p_first=11)
     assert np.allclose(to_numpy(dmu), 0.75 * odmu, rtol=GRAD_TOL, atol=0)
     assert dsig.item() == pytest.approx(0.75 * odsig, rel=GRAD_TOL)
-    np.testing.assert_allclose(to_numpy(dx0), 0.75 * odx0, rtol=GRAD_TOL, atol=1e-12)
+    # dx0 = g k x_T / P inherits the position error absolutely (near x_T = 0
+    # the relative bar does not apply; the propagated one does).
+    np.testing.assert_allclose(to_numpy(dx0), 0.75 * odx0, rtol=GRAD_TOL, atol=0.75 * 2.0 / (5 * n) * POS_TOL)
 
 
 def test_walk3d_autograd_function(torch_cuda, orc):
@@ -134,7 +136,7 @@ def test_walk3d_autograd_function(torch_cuda, orc):
     assert loss.item() == pytest.approx(orc.walk3d_loss(oxT, 2.0, n), rel=1e-6)
     assert np.allclose(mu.grad.numpy(), odmu, rtol=GRAD_TOL)
     assert sigma.grad.item() == pytest.approx(odsig, rel=GRAD_TOL)
-    np.testing.assert_allclose(to_numpy(x0.grad), odx0, rtol=GRAD_TOL)
+    np.testing.assert_allclose(to_numpy(x0.grad), odx0, rtol=GRAD_TOL, atol=2.0 / n * POS_TOL)
     # Central differences through the GPU forward agree with the adjoint.
     h = 1e-3
     with torch.no_grad():
@@ -197,7 +199,7 @@ def test_walk3d_full_workload(torch_cuda, orc):
                                       want_ckpt=True)
         pos_close(gx[q:q + 1], oxT)
         pos_close(to_numpy(ck[:, q]), ock[:, 0])
-        np.testing.assert_allclose(gdx[q], c["k"] * oxT[0] / P, rtol=GRAD_TOL)
+        np.testing.assert_allclose(gdx[q], c["k"] * oxT[0] / P, rtol=GRAD_TOL, atol=c["k"] / P * POS_TOL)
     # Properties of the full run (exact identities of the linear walk).
     x64 = xT.double()
     assert loss.item() == pytest.approx(0.5 * c["k"] * (x64 ** 2).sum().item() / P, rel=1e-9)
@@ -380,3 +382,37 @@ def test_walk3d_stored_full_steps_subset(torch_cuda, orc):
     odmu, odsig, _ = orc.walk3d_adjoint(c["seed"], 512, T, dt32, oxT, c["k"], c["n_particles"], p_first=777, threads=8)
     assert np.allclose(to_numpy(sdmu), 0.5 * odmu, rtol=GRAD_TOL)
     assert sdsig.item() == pytest.approx(0.5 * odsig, rel=GRAD_TOL)
+
+
+# --------------------------------------------------- cuRAND comparison ----
+
+def test_walk2d_curand_forms_agree_and_diffuse(torch_cuda):
+    """cuRAND's Philox walk, per-step (Fig. 2) and fused: the same cuRAND
+    draws, so the same positions up to summation order; at 0 steps the
+    start positions match exactly; the fused walk obeys Einstein's relation."""
+    torch = torch_cuda
+    sh = torch.cuda.current_stream().cuda_stream
+    n, steps = 5000 + 17, 300
+    p = orand.walk2d_params(n, steps, dt=1e-3, D=1.0, p_first=123)
+    states = torch.empty(n * orand.orand_walk2d_curand_state_bytes(), dtype=torch.uint8, device="cuda")
+    pos_a = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    pos_b = torch.empty_like(pos_a)
+    orand.orand_walk2d_curand_setup(p, states.data_ptr(), pos_a.data_ptr(), 1984, sh)
+    p0 = orand.walk2d_params(n, 0, dt=1e-3, D=1.0, p_first=123)
+    orand.orand_walk2d_curand_fused(p0, pos_b.data_ptr(), 1984, sh)
+    torch.cuda.synchronize()
+    assert torch.equal(pos_a, pos_b)
+    orand.orand_walk2d_curand_run(p, states.data_ptr(), pos_a.data_ptr(), sh)
+    orand.orand_walk2d_curand_fused(p, pos_b.data_ptr(), 1984, sh)
+    torch.cuda.synchronize()
+    assert torch.allclose(pos_a, pos_b, rtol=POS_TOL, atol=POS_TOL)
+    m, T = 1 << 20, 1000
+    big = orand.walk2d_params(m, T, dt=1e-3, D=1.0)
+    start = torch.empty((m, 2), dtype=torch.float32, device="cuda")
+    end = torch.empty_like(start)
+    orand.orand_walk2d_curand_fused(orand.walk2d_params(m, 0), start.data_ptr(), 7, sh)
+    orand.orand_walk2d_curand_fused(big, end.data_ptr(), 7, sh)
+    torch.cuda.synchronize()
+    var = (end.double() - start.double()).var(dim=0).cpu().numpy()
+    expect = 2 * 1.0 * T * _f32(1e-3)
+    assert np.all(np.abs(var / expect - 1) < 5 * math.sqrt(2 / m))
