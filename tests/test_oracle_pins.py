@@ -145,25 +145,23 @@ def test_tyche_words_are_b_after_each_mix(orc):
 _TF_ROT = [(10, 26), (11, 21), (13, 27), (23, 5), (6, 20), (17, 11), (25, 10), (18, 20)]
 
 
-def _skein_c240():
-    """Skein's key-schedule parity constant C240, derived as Skein does: the
-    AES-256 encryption, under the all-zero key, of the number 240 (a 16-byte
-    big-endian block); C240 is the last 8 bytes of the result.  AES comes
-    from the ``cryptography`` package, outside this project."""
+# Threefry's 32-bit key-schedule parity word (the high half of Skein's C240).
+_TF_PARITY = 0x1BD11BDA
+
+
+def test_threefry_parity_constant_is_skein_c240():
+    """Skein derives C240 as the AES-256 encryption, under the all-zero key,
+    of the number 240 (a 16-byte big-endian block): the last 8 bytes of the
+    result.  AES comes from the ``cryptography`` package, outside this
+    project; Threefry's parity word is C240's high half."""
+    pytest.importorskip("cryptography")
     from cryptography.hazmat.primitives.ciphers import Cipher, algorithms, modes
 
     enc = Cipher(algorithms.AES(bytes(32)), modes.ECB()).encryptor()
     ct = enc.update((240).to_bytes(16, "big")) + enc.finalize()
-    return int.from_bytes(ct[8:], "big")
-
-
-# Threefry's 32-bit parity word is the high half of C240.
-_TF_PARITY = _skein_c240() >> 32
-
-
-def test_threefry_parity_constant_is_skein_c240():
-    assert _skein_c240() == 0x1BD11BDAA9FC1A22
-    assert _TF_PARITY == 0x1BD11BDA
+    c240 = int.from_bytes(ct[8:], "big")
+    assert c240 == 0x1BD11BDAA9FC1A22
+    assert c240 >> 32 == _TF_PARITY
 
 
 def _rotr(x, r):
