@@ -170,6 +170,21 @@ def fill_rows(torch, orand, W, rank):
 
             rows.append(Row("fill/%s/%s" % (W.GEN_NAMES[gen], W.DTYPE_NAMES[dt]), run, nbytes, "B", 1,
                             bytes_written=nbytes))
+    # The small Philox fill (2^16 streams x 64 draws, 16 MiB per dtype): it
+    # stays in the 126 MB L2, so the launch's latency is what is measured.
+    cs = W.FILL_SMALL
+    s_seed = cs["seed"] ^ (rank * cs["n_streams"])
+    for dt in (W.U32, W.F32_UNIFORM):
+        out = torch.empty(cs["n_streams"] * cs["dps"], dtype=orand.torch_dtype(dt), device="cuda")
+        bufs[("small", dt)] = out
+        nbytes = out.numel() * out.element_size()
+
+        def run_small(sh, dt=dt, out=out):
+            orand.orand_fill(W.PHILOX, dt, s_seed, cs["counter"], cs["n_streams"], cs["dps"], out.data_ptr(), sh)
+
+        row = Row("fill_small/philox4x32_10/%s" % W.DTYPE_NAMES[dt], run_small, nbytes, "B", 1)
+        row.extra = {"note": "16 MiB, L2-resident: launch latency, not HBM"}
+        rows.append(row)
     return rows, bufs
 
 

@@ -12,14 +12,18 @@
 //     chunks of `chunk_values` values.  A warp takes one chunk at a time; its
 //     32 lanes write consecutive 16-byte groups, and per-stream setup (round
 //     keys, Squares key hash) is paid once per chunk.
-// Warps claim work through two atomic cursors (Tyche items first, then
-// chunks).  There are no inter-block waits.
+// Warps take Tyche items and chunks through two atomic cursors.  The
+// latency-bound Tyche chains get a few SMs of their own (four chain warps
+// each) so that compute-heavy chunk warps do not slow them; the other SMs
+// take the chunks, then the Tyche items left.  There are no inter-block
+// waits.
 //
 // Autotuning: block size, chunk size and store width (16/8/4-byte stores)
 // are timed on the caller's batch the first time a size class is seen.  The
 // output is written again each time with the same bits.  The fastest
 // configuration is kept per size class in the context.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -55,7 +59,7 @@ struct RaggedHeader {
     uint64_t n_conv_items;
     uint64_t conv_chunk_groups;                            // groups per convert item
     uint32_t n_ty_items;                                   // Tyche warp items (32 slots each)
-    uint32_t pad;
+    uint32_t tyche_warps;                                  // warps to give the Tyche chains SMs of their own
 };
 static_assert(sizeof(RaggedHeader) <= 256, "header slot");
 constexpr uint32_t kNoRequest = 0xFFFFFFFFu;
@@ -103,6 +107,16 @@ __device__ __forceinline__ uint4 tyche_next4(orand::TycheState &st)
 // produces the words of batch k+1, the independent conversion and stores of
 // batch k fill the issue slots the chain leaves idle.
 constexpr int kTycheBatch = 4;
+
+// Device table tail: the two work cursors, then the scheduler gates.
+constexpr size_t kCursorBytes = 256;
+constexpr unsigned kGateSlots = 1024;  // per-SM arrival counters, by SM id (folded)
+// Chain warps per Tyche SM.  Measured on B300: chains alone keep full speed
+// up to 8 warps per SM, but each lane's 16-byte store to its own request
+// (32 distinct lines per warp store) saturates the SM's store path beyond
+// 4 warps (65.7 ns per MIX at 8 against 31.5 at 4).
+constexpr unsigned kTycheWarpsPerSm = 4;
+constexpr size_t kCursorAreaBytes = kCursorBytes + kGateSlots * sizeof(unsigned);
 
 template <int DT, int SW>
 __device__ __forceinline__ void tyche_request(const RaggedReq &q, char *out)
@@ -194,22 +208,54 @@ __global__ void ragged_kernel(char *table)
     const uint32_t *tyche = reinterpret_cast<const uint32_t *>(table + h.off_tyche);
     unsigned long long *cursors = reinterpret_cast<unsigned long long *>(table + h.off_cursors);
     const int lane = threadIdx.x & 31;
-    // Phase 1: Tyche warp items (32 requests of one dtype), longest first.
-    for (;;) {
-        unsigned long long wi = 0;
-        if (lane == 0) wi = atomicAdd(&cursors[0], 1ull);
-        wi = __shfl_sync(0xFFFFFFFFu, wi, 0);
-        if (wi >= h.n_ty_items) break;
-        const uint32_t r = tyche[wi * 32 + lane];
-        if (r != kNoRequest) {
-            // A register copy: the output stores could alias the table as far
-            // as the compiler knows, so a reference would be re-read from
-            // global memory inside the chain loop.
-            const RaggedReq q = reqs[r];
-            tyche_request_rt<SW>(q, h.out);
+    unsigned *sm_rank = reinterpret_cast<unsigned *>(table + h.off_cursors + kCursorBytes);
+    // Tyche warp items (32 requests of one dtype, longest first) come from
+    // cursor 0.  Each chain is one latency-bound dependency chain: up to
+    // two per scheduler run at full speed, but compute-heavy warps on the
+    // same SM (the chunks) slow it two- to four-fold, and so do more than
+    // kTycheWarpsPerSm chains on one SM (their scattered stores).  So the
+    // chains get SMs of their own: K SMs, spread by SM id, on which the first
+    // kTycheWarpsPerSm warps to arrive take Tyche items (then chunks) and the
+    // other warps leave.  On every other SM all warps take chunks first; then the first
+    // two warps to have arrived take the Tyche items still left.  Each item
+    // is claimed once, through the cursor, whoever takes it.
+    unsigned rank = 0, tyche_sm = 0;
+    if (lane == 0) {
+        unsigned smid, nsmid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+        rank = atomicAdd(&sm_rank[smid & (kGateSlots - 1u)], 1u);
+        const unsigned cap = nsmid / 2 > 1u ? nsmid / 2 : 1u;
+        const unsigned want = (h.tyche_warps + kTycheWarpsPerSm - 1) / kTycheWarpsPerSm;
+        const unsigned K = want < cap ? want : cap;
+        if (K) {
+            const unsigned stride = nsmid / K > 1u ? nsmid / K : 1u;
+            tyche_sm = smid % stride == 0 && smid / stride < K;
         }
     }
-    // Phase 2: chunks of the random-access requests.
+    rank = __shfl_sync(0xFFFFFFFFu, rank, 0);
+    tyche_sm = __shfl_sync(0xFFFFFFFFu, tyche_sm, 0);
+    auto tyche_items = [&]() {
+        for (;;) {
+            unsigned long long wi = 0;
+            if (lane == 0) wi = atomicAdd(&cursors[0], 1ull);
+            wi = __shfl_sync(0xFFFFFFFFu, wi, 0);
+            if (wi >= h.n_ty_items) break;
+            const uint32_t r = tyche[wi * 32 + lane];
+            if (r != kNoRequest) {
+                // A register copy: the output stores could alias the table as
+                // far as the compiler knows, so a reference would be re-read
+                // from global memory inside the chain loop.
+                const RaggedReq q = reqs[r];
+                tyche_request_rt<SW>(q, h.out);
+            }
+        }
+    };
+    if (tyche_sm) {
+        if (rank >= kTycheWarpsPerSm) return;
+        tyche_items();
+    }
+    // Chunks of the random-access requests.
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(&cursors[1], 1ull);
@@ -226,6 +272,7 @@ __global__ void ragged_kernel(char *table)
         default: chunk_dt<ORAND_SQUARES32, SW>(q, h.out, g0, g1, lane); break;
         }
     }
+    if (!tyche_sm && rank < 2) tyche_items();
 }
 
 // In-place conversion of the raw words Tyche lanes stored: each warp takes
@@ -336,6 +383,7 @@ struct Plan {
     std::vector<RaggedReq> reqs;
     std::vector<uint32_t> tyche;  // warp items of 32 slots, kNoRequest-padded
     uint64_t n_tyche = 0;
+    uint32_t tyche_warps = 0;     // warps the Tyche chains should get (0: no Tyche requests)
     uint64_t n_items = 0;
     uint64_t total_values = 0;
     size_t off_reqs = 256, off_items = 0, off_tyche = 0, off_conv = 0, off_cursors = 0, table_bytes = 0;
@@ -422,6 +470,15 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
     }
     std::stable_sort(items.begin(), items.end(),
                      [](const WarpItem &a, const WarpItem &b) { return a.longest > b.longest; });
+    // Warps for the chains: the longest item sets the floor of the batch's
+    // time, so aim for about twice the total item cost over the longest.
+    p->tyche_warps = 0;
+    if (!items.empty()) {
+        double total = 0.0;
+        for (const WarpItem &w : items) total += (double)w.longest;
+        const double want = 2.0 * total / (double)items.front().longest;
+        p->tyche_warps = (uint32_t)std::min<double>((double)items.size(), std::max(8.0, std::ceil(want)));
+    }
     p->tyche.assign(items.size() * 32, kNoRequest);
     for (size_t w = 0; w < items.size(); ++w)
         for (uint32_t l = 0; l < 32 && items[w].first + l < ty[items[w].dtype].size(); ++l)
@@ -431,7 +488,7 @@ static orand_status_t plan_requests(const orand_request_t *r, size_t n, const ch
     p->off_tyche = align_up(p->off_items + p->n_items * sizeof(uint32_t), 256);
     p->off_conv = align_up(p->off_tyche + p->tyche.size() * sizeof(uint32_t), 256);
     p->off_cursors = align_up(p->off_conv + p->conv.size() * sizeof(uint32_t), 256);
-    p->table_bytes = p->off_cursors + 256;
+    p->table_bytes = p->off_cursors + kCursorAreaBytes;
     return ORAND_OK;
 }
 
@@ -446,6 +503,7 @@ static void write_staging(const Plan &p, char *out, char *h)
     hd.off_tyche = p.off_tyche;
     hd.off_cursors = p.off_cursors;
     hd.n_ty_items = (uint32_t)(p.tyche.size() / 32);
+    hd.tyche_warps = p.tyche_warps;
     hd.off_conv = p.off_conv;
     hd.n_conv_items = p.conv.size();
     hd.conv_chunk_groups = kConvChunkGroups;
@@ -462,7 +520,7 @@ static void write_staging(const Plan &p, char *out, char *h)
     }
     std::memcpy(h + p.off_tyche, p.tyche.data(), p.tyche.size() * sizeof(uint32_t));
     std::memcpy(h + p.off_conv, p.conv.data(), p.conv.size() * sizeof(uint32_t));
-    std::memset(h + p.off_cursors, 0, 256);
+    std::memset(h + p.off_cursors, 0, kCursorAreaBytes);
 }
 
 // Bytes the graph copies: the table rounded up to a power of two, so batches
@@ -585,7 +643,7 @@ static orand_status_t autotune(RaggedState *s, const orand_request_t *r, size_t 
                 cand.ctas_per_sm = 0;
                 unsigned grid = 0;
                 if ((st = ragged_grid(cand, &grid)) != ORAND_OK) break;
-                cudaMemsetAsync((char *)s->d_tables + p.off_cursors, 0, 16, stream);
+                cudaMemsetAsync((char *)s->d_tables + p.off_cursors, 0, kCursorAreaBytes, stream);
                 cudaEventRecord(a, stream);
                 launch_kernel((char *)s->d_tables, cand, grid, stream);
                 if ((st = launch_status()) != ORAND_OK) break;
