@@ -13,8 +13,8 @@
 //     32 lanes write consecutive 16-byte groups, and per-stream setup (round
 //     keys, Squares key hash) is paid once per chunk.
 // Warps take Tyche items and chunks through two atomic cursors.  The
-// latency-bound Tyche chains get a few SMs of their own (four chain warps
-// each) so that compute-heavy chunk warps do not slow them; the other SMs
+// latency-bound Tyche chains get SMs of their own (two chain warps each) so
+// that compute-heavy chunk warps do not slow them; the other SMs
 // take the chunks, then the Tyche items left.  There are no inter-block
 // waits.
 //
@@ -113,9 +113,12 @@ constexpr size_t kCursorBytes = 256;
 constexpr unsigned kGateSlots = 1024;  // per-SM arrival counters, by SM id (folded)
 // Chain warps per Tyche SM.  Measured on B300: chains alone keep full speed
 // up to 8 warps per SM, but each lane's 16-byte store to its own request
-// (32 distinct lines per warp store) saturates the SM's store path beyond
-// 4 warps (65.7 ns per MIX at 8 against 31.5 at 4).
-constexpr unsigned kTycheWarpsPerSm = 4;
+// (32 distinct lines per warp store) loads the SM's store path: alone, 4
+// warps per SM still ran at full speed and 8 at half; inside the
+// 100,000-request batch, with the chunk warps' write traffic on the other
+// SMs, 4 per SM gave 40-51 ms (run to run) and 2 per SM 31-33 ms, at the
+// 29.6 ms floor of the longest chain.
+constexpr unsigned kTycheWarpsPerSm = 2;
 constexpr size_t kCursorAreaBytes = kCursorBytes + kGateSlots * sizeof(unsigned);
 
 template <int DT, int SW>
