@@ -8,7 +8,9 @@
 
 Each case launches its kernels `--reps` times on the current stream.  Every
 launch is timed with CUDA events, and one line per case is printed with the
-mean time and the case's own throughput unit.  The sizes are free, so an ncu
+mean time and the case's own throughput unit.  The ragged cases queue 100 ms
+of GPU work before each timed call, so the host's planning of the batch
+overlaps it and the events measure GPU time.  The sizes are free, so an ncu
 capture can target one kernel at a small size (`-k`, `-c`).
 """
 from __future__ import annotations
@@ -20,9 +22,15 @@ import statistics
 import numpy as np
 
 
-def timed(torch, fn, reps):
+def timed(torch, fn, reps, busy_ms=0.0):
+    """Event-timed launches.  busy_ms > 0 first queues that much GPU work
+    (torch.cuda._sleep), so host-side preparation inside fn (the ragged
+    batch's planning) overlaps it, as it does in a step with work queued
+    ahead, and the events measure GPU time only."""
     ts = []
     for _ in range(reps):
+        if busy_ms > 0:
+            torch.cuda._sleep(int(busy_ms * 1e-3 * 2.0e9))
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
@@ -100,7 +108,7 @@ def main(argv=None):
         fn = lambda: orand.orand_fill_ragged(ctx, recs.ctypes.data, len(recs), out.data_ptr(), total, sh)
         fn()  # first call tunes its size class
         torch.cuda.synchronize()
-        ts = timed(torch, fn, args.reps)
+        ts = timed(torch, fn, args.reps, busy_ms=100.0)
         values = int(recs["length"].sum())
         res.update(requests=len(recs), values=values, ms=statistics.mean(ts),
                    values_per_s=values / (statistics.mean(ts) * 1e-3),
