@@ -73,3 +73,56 @@ def test_two_rank_sharding_matches_unsharded(orc):
     for rank, fill, red in res:
         assert np.array_equal(fill, full_fill)
         assert np.allclose(red, want, rtol=1e-12, atol=0)
+
+
+def _stream_worker(rank, world, port, q):
+    """The parallel-stream battery sharded by iteration range: rank r counts
+    the micro-streams of iterations [r*I, (r+1)*I) and the counts are summed
+    over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    from oracle import stream_stats as S
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n_part, draws, iters = 200, 3, 32                  # 32 iterations: whole birthday samples
+        w = S.micro_stream_words(0, 0, n_part, draws, rank * iters, iters)
+        tup = S.tuple_counts(w, 3, 4, 28, 3).astype(np.int64)
+        bday = S.birthday_counts(w, 6, 16, 0, 40).astype(np.int64)
+        gaps, _ = S.gap_counts(w, 0, 1 << 28, 64)
+        t = torch.from_numpy(np.concatenate([tup, bday, gaps.astype(np.int64)]))
+        dist.all_reduce(t)
+        q.put((rank, t.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_stream_battery_matches_one_stream():
+    """Summed over ranks, tuple and birthday counts equal those of the whole
+    stream (each rank's share is a multiple of 32 iterations, so no tuple or
+    sample straddles a rank boundary); the gap counts miss exactly the gap
+    that spans each rank boundary."""
+    from oracle import stream_stats as S
+
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_stream_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=240) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = S.micro_stream_words(0, 0, 200, 3, 0, 32 * world)
+    tup = S.tuple_counts(w, 3, 4, 28, 3).astype(np.int64)
+    bday = S.birthday_counts(w, 6, 16, 0, 40).astype(np.int64)
+    gaps, _ = S.gap_counts(w, 0, 1 << 28, 64)
+    nt, nb = tup.size, bday.size
+    for rank, red in res:
+        assert np.array_equal(red[:nt], tup)
+        assert np.array_equal(red[nt:nt + nb], bday)
+        assert int(gaps.astype(np.int64).sum() - red[nt + nb:].sum()) == world - 1
