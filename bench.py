@@ -42,12 +42,12 @@ METRIC = "Philox u32 fill GB/s vs HBM peak; walk particle-steps/s; adjoint vs pl
 ALU_PEAK = 148 * 128 * 2.032e9
 # Algorithmic operations per 2D particle-step, counted from the kernel source:
 # Philox4x32-10 with the two used words and the constant counter words
-# folded (33), the walks' Box-Muller radius (20: u1 and v, the six-term
+# folded (33), the walks' Box-Muller radius (19: u1 and v, the six-term
 # series, the log2 estimate, the selection and the square root) and angle
 # (19: quadrant reduction, sin and cos estimates, swap and signs), the step
 # scale, two FMA sums, the step loop shared by two particles and the Kahan
 # add of each 16-step block sum (5).
-WALK2D_OPS_PER_STEP = 77
+WALK2D_OPS_PER_STEP = 76
 
 
 def parse_args():

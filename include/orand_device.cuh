@@ -447,7 +447,10 @@ __device__ __forceinline__ float bm_radius_walk(uint32_t w0)
     const float x_series = 2.0f * v * p;
     const float x_log = -1.3862943611198906f * sfu_lg2(u1);   /* -2 ln 2 log2(u1) */
     const float x = v < 0.0625f ? x_series : x_log;
-    return x > 0.0f ? x * sfu_rsqrt(x) : 0.0f;
+    /* x is +0 (u1 = 1) or at least about 1.2e-7: the floor only turns
+     * rsqrt(0) = inf into a finite factor, so x = 0 gives 0 without a
+     * compare and select. */
+    return x * sfu_rsqrt(fmaxf(x, 1.17549435e-38f));
 }
 
 /* (cos, sin)(2 pi u2), u2 = (w1 >> 8) 2^-24, by the exact quadrant
