@@ -416,3 +416,41 @@ def test_walk2d_curand_forms_agree_and_diffuse(torch_cuda):
     var = (end.double() - start.double()).var(dim=0).cpu().numpy()
     expect = 2 * 1.0 * T * _f32(1e-3)
     assert np.all(np.abs(var / expect - 1) < 5 * math.sqrt(2 / m))
+
+
+def test_walk3d_ou_full_workload(torch_cuda, orc):
+    """The OU walk in the bench's configuration (2^22 x 4096, kappa = 1):
+    sampled particles (positions, checkpoints, dx0) against the FP64 oracle,
+    the loss identity over all particles, and a particle-range subset of the
+    reductions (dmu, dsigma, dkappa) against the oracle adjoint."""
+    torch = torch_cuda
+    c = W.WALK3D_OU
+    P, T, K = c["n_particles"], c["steps"], c["ckpt_every"]
+    p = orand.walk3d_params(P, T, c["dt"], c["mu"], c["sigma"], c["k"], c["seed"], K, kappa=c["kappa"])
+    xT, ck, loss = orand.walk3d_forward(p)
+    dmu, dsig, dkap, dx0 = orand.walk3d_backward_full(p, xT, ck)
+    torch.cuda.synchronize()
+    dt32 = _f32(c["dt"])
+    rng = np.random.default_rng(21)
+    ids = np.unique(np.concatenate([[0, P - 1], rng.integers(0, P, 14)]))
+    gx, gdx = to_numpy(xT), to_numpy(dx0)
+    for q in ids:
+        oxT, ock, xs = orc.walk3d_ou_forward(c["seed"], 1, T, K, dt32, c["mu"], c["sigma"], c["kappa"],
+                                             p_first=int(q), want_ckpt=True)
+        pos_close(gx[q:q + 1], oxT)
+        pos_close(to_numpy(ck[:, q]), ock[:, 0])
+        _, _, _, odx0 = orc.walk3d_ou_adjoint(c["seed"], 1, T, dt32, c["kappa"], xs, c["k"], P, p_first=int(q))
+        np.testing.assert_allclose(gdx[q], odx0[0], rtol=GRAD_TOL, atol=c["k"] / P * POS_TOL)
+    x64 = xT.double()
+    assert loss.item() == pytest.approx(0.5 * c["k"] * (x64 ** 2).sum().item() / P, rel=1e-9)
+    assert np.all(np.isfinite(to_numpy(dmu))) and np.isfinite(dsig.item()) and np.isfinite(dkap.item())
+    sub = orand.walk3d_params(1024, T, c["dt"], c["mu"], c["sigma"], c["k"], c["seed"], K, p_first=654321,
+                              p_total=P, kappa=c["kappa"])
+    sxT, sck, _ = orand.walk3d_forward(sub)
+    sdmu, sdsig, sdk, _ = orand.walk3d_backward_full(sub, sxT, sck)
+    torch.cuda.synchronize()
+    _, _, xs = orc.walk3d_ou_forward(c["seed"], 1024, T, K, dt32, c["mu"], c["sigma"], c["kappa"], p_first=654321)
+    odmu, odsig, odk, _ = orc.walk3d_ou_adjoint(c["seed"], 1024, T, dt32, c["kappa"], xs, c["k"], P, p_first=654321)
+    assert np.allclose(to_numpy(sdmu), odmu, rtol=GRAD_TOL)
+    assert sdsig.item() == pytest.approx(odsig, rel=GRAD_TOL)
+    assert sdk.item() == pytest.approx(odk, rel=GRAD_TOL)
