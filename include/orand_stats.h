@@ -71,8 +71,9 @@ orand_status_t orand_stat_gaps(orand_ctx_t ctx, const uint32_t *words, uint64_t 
  * word's birthday is (w >> shift) & (2^bits - 1) in a year of m = 2^bits
  * days.  With the birthdays sorted, Y(1) <= ... <= Y(n), the n spacings are
  * Y(i+1) - Y(i) and Y(1) + m - Y(n); sorted, R = the number of j with
- * S(j) == S(j-1).  counts[min(R, r_max)] += 1 per sample.  R is close to
- * Poisson with mean n^3 / (4 m) for a good generator.
+ * S(j) == S(j-1).  counts[min(R, r_max)] += 1 per sample.  For a good
+ * generator R has mean n(n-1)^2/(4m) - n(n-1)^2(n-2)^2/(18m^2) (equal pairs
+ * minus triples; Knuth's n^3/(4m) to first order) and is close to Poisson.
  * log2_n: 2..12, bits: 1..32, shift + bits <= 32, r_max: 1..4096.
  * counts: r_max + 1 uint64, 8-byte aligned.
  * Errors: INVALID_ARG, ALIGNMENT, CUDA. */
