@@ -762,7 +762,7 @@ def main():
                        "parallelism": "dp%d (disjoint stream ranges per rank)" % world},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "fill_tile_kernel<philox4x32_10, u32, R=4> (TMA tile store)",
+                         "kernel": "fill_tile_kernel<philox4x32_10, u32, R=4> (swizzled tile, TMA tensor store)",
                          "peak_kind": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"},
             "rooflines": rooflines,
             "clocks": clocks,

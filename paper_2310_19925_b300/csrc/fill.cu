@@ -11,6 +11,9 @@
 // resident capacity of the 148 SMs and strides over the groups.
 #include <cstdlib>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 #include "orand_device.cuh"
 #include "values.cuh"
@@ -57,39 +60,55 @@ __global__ void __launch_bounds__(256) fill_random_access_kernel(FillArgs a)
 // Philox round keys, the Threefry key schedule, the Squares key hash) is paid
 // once per R groups.  Runs are consecutive in memory.  A CTA of T threads
 // fills one contiguous tile of T * TR runs (TR runs per thread) in shared
-// memory, and one thread streams it to HBM with a bulk asynchronous copy
-// (cp.async.bulk, the TMA engine).  The copy is double-buffered, so the next
-// tile is generated while the previous one drains.
+// memory, and one thread writes it to HBM with a TMA tensor store
+// (cp.async.bulk.tensor).  The copy is double-buffered, so the next tile is
+// generated while the previous one drains.
+//
+// The output is viewed as a 2D tensor of 128-byte rows, and the tensor map
+// uses the 128-byte swizzle: 16-byte chunk c of tile row y sits at shared
+// offset y * 128 + ((c ^ (y % 8)) * 16).  A run is R chunks of one row
+// (R <= 8, runs aligned to R chunks), so a thread's chunk i lands at
+// a0 ^ (i * 16) for one base a0, and the eight threads of each 128-byte
+// shared-store phase hit eight distinct bank groups for every R.  So the
+// group index stays the unrolled loop's constant i, and when each stream is a
+// single run, Philox's first two rounds fold across the R blocks of a stream
+// at compile time (measured on B300: 7 % faster than rotating the group order
+// per thread to avoid the bank conflicts of an unswizzled tile).  Rows past
+// the last full row are clipped by the tensor store; the chunks of a final
+// partial row (fewer than 8) are stored directly by the threads that make
+// them.
 //
 // Launch shape per row (measured on B300): the light, HBM-bound Philox u32 and
 // FP32-uniform fills use T = 128 and TR = 8 / R, which halves the per-tile
 // barrier and bookkeeping cost per group.  Every other fill is bound by the
 // integer or FMA pipes and keeps T = 256, TR = 1, for more warps per SM.
-//
-// Shared-memory bank conflicts: thread x writes 16-byte slots (k*T + x)*R + j.
-// At step i it handles j = (i + (x >> log2(8/R))) mod R, which puts the eight
-// threads of each 128-byte store phase on eight distinct bank groups.  k*T*R
-// slots is a multiple of 128 bytes, so each extra run keeps the pattern.
 
-__device__ __forceinline__ void bulk_store_s2g(void *gdst, const void *ssrc, uint32_t bytes)
+__device__ __forceinline__ void tensor_store_2d(const CUtensorMap *map, uint32_t smem, int x, int y)
 {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
+                 "r"(smem), "r"(x), "r"(y)
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v)
+{
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
 
 struct TileArgs {
     uint64_t seed;
-    uint64_t n_runs;      // n_streams * G / R
-    uint64_t n_tiles;     // ceil(n_runs / (T * TR))
-    uint64_t rps;         // runs per stream = G / R
-    int rps_shift;        // log2(rps) when rps is a power of two, else -1
+    uint64_t r_first;      // global index of this launch's first run
+    uint64_t n_runs;       // runs of this launch
+    uint64_t n_tiles;      // ceil(n_runs / (T * TR))
+    uint64_t full_chunks;  // 16-byte chunks in the full 128-byte rows of this launch's output
+    uint64_t rps;          // runs per stream = G / R
+    int rps_shift;         // log2(rps) when rps is a power of two, else -1
     uint32_t counter;
-    uint4 *out;           // 16-byte aligned
+    uint4 *out;            // run r_first's first chunk; 16-byte aligned
 };
 
 // Per-stream state of a random-access generator, set up once per run.
@@ -124,11 +143,13 @@ struct StreamGen<ORAND_SQUARES32> {
     __device__ __forceinline__ uint4 group(uint32_t b) const { return orand::squares_block(key, counter, b); }
 };
 
-// Run r: groups [q*R, q*R + R) of stream s, written to slots [slot*R, slot*R + R).
+// Run lr of this launch (global run r = r_first + lr): groups [q*R, q*R + R)
+// of stream s.  Chunk i goes to the shared address a0 ^ (i * 16) and, when
+// the run lies in a final partial row, straight to HBM as well.
 template <int GEN, int DT, int R>
-__device__ __forceinline__ void fill_run(const TileArgs &a, uint64_t r, int x, uint4 *sm, uint64_t slot)
+__device__ __forceinline__ void fill_run(const TileArgs &a, uint64_t lr, uint32_t a0)
 {
-    constexpr int ROT_SHIFT = R == 8 ? 0 : R == 4 ? 1 : R == 2 ? 2 : 3;
+    const uint64_t r = a.r_first + lr;
     uint64_t s, q;
     if (a.rps_shift >= 0) {
         s = r >> a.rps_shift;
@@ -137,53 +158,69 @@ __device__ __forceinline__ void fill_run(const TileArgs &a, uint64_t r, int x, u
         s = r / a.rps;
         q = r - s * a.rps;
     }
+    const bool tail = lr * R >= a.full_chunks;
+    uint4 *gout = a.out + lr * R;
+    auto put = [&](int i, uint4 bits) {
+        st_shared_v4(a0 ^ ((uint32_t)i << 4), bits);
+        if (tail) gout[i] = bits;
+    };
     if constexpr (GEN == ORAND_TYCHE) {
-        // Whole stream in one run (R == G): sequential words, slot order.
+        // Whole stream in one run (R == G): sequential words.
         orand::TycheState st = orand::tyche_init(a.seed ^ s, a.counter);
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
+        for (int i = 0; i < R; ++i) {
             uint4 w;
             w.x = orand::tyche_next(st);
             w.y = orand::tyche_next(st);
             w.z = orand::tyche_next(st);
             w.w = orand::tyche_next(st);
-            sm[slot * R + j] = group_bits<DT>(w);
+            put(i, group_bits<DT>(w));
         }
     } else {
         const StreamGen<GEN> sg(a.seed ^ s, a.counter);
-        const uint32_t b0 = (uint32_t)(q * R);
+        if (a.rps == 1) {
+            // Every stream is one run (the same for the whole launch): the
+            // group indices are the constants 0..R-1.
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const int j = (i + (x >> ROT_SHIFT)) & (R - 1);
-            sm[slot * R + j] = group_bits<DT>(sg.group(b0 + (uint32_t)j));
+            for (int i = 0; i < R; ++i) put(i, group_bits<DT>(sg.group((uint32_t)i)));
+        } else {
+            const uint32_t b0 = (uint32_t)(q * R);
+#pragma unroll
+            for (int i = 0; i < R; ++i) put(i, group_bits<DT>(sg.group(b0 + (uint32_t)i)));
         }
     }
 }
 
 template <int GEN, int DT, int R, int T, int TR>
-__global__ void __launch_bounds__(T) fill_tile_kernel(TileArgs a)
+__global__ void __launch_bounds__(T) fill_tile_kernel(const __grid_constant__ CUtensorMap map, TileArgs a)
 {
-    constexpr uint64_t kRunsPerTile = (uint64_t)T * TR;
-    extern __shared__ __align__(128) uint4 tile[];          // 2 buffers of kRunsPerTile * R groups
-    const int x = threadIdx.x;
+    constexpr uint32_t kRunsPerTile = (uint32_t)T * TR;
+    constexpr uint32_t kTileBytes = kRunsPerTile * R * 16;
+    constexpr uint32_t kTileRows = kTileBytes / 128;
+    static_assert(kTileBytes % 1024 == 0 && kTileRows <= 256, "a tile is whole swizzle periods, at most 256 rows");
+    // Two tile buffers from a 1024-byte boundary (the 128-byte swizzle's period);
+    // the launch adds 1 KiB of slack for the round-up.
+    extern __shared__ __align__(1024) uint8_t tile_raw[];
+    const uint32_t base = ((uint32_t)__cvta_generic_to_shared(tile_raw) + 1023u) & ~1023u;
+    const uint32_t x = threadIdx.x;
     int buf = 0;
     for (uint64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        uint4 *sm = tile + buf * (kRunsPerTile * R);
-        // The bulk copy issued two tiles ago read this buffer; wait until it has.
+        const uint32_t sb = base + (uint32_t)buf * kTileBytes;
+        // The tensor store issued two tiles ago read this buffer; wait until it has.
         if (x == 0) bulk_wait_read_1();
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < TR; ++k) {
-            const uint64_t slot = (uint64_t)k * T + x;
-            const uint64_t r = t * kRunsPerTile + slot;
-            if (r < a.n_runs) fill_run<GEN, DT, R>(a, r, x, sm, slot);
+            const uint32_t slot = (uint32_t)k * T + x;
+            const uint32_t row = (slot * R) >> 3;
+            const uint32_t a0 = sb + row * 128u + ((((slot * R) & 7u) ^ (row & 7u)) << 4);
+            const uint64_t lr = t * kRunsPerTile + slot;
+            if (lr < a.n_runs) fill_run<GEN, DT, R>(a, lr, a0);
         }
         fence_proxy_async_smem();
         __syncthreads();
         if (x == 0) {
-            const uint64_t r0 = t * kRunsPerTile;
-            const uint64_t runs = min(kRunsPerTile, a.n_runs - r0);
-            bulk_store_s2g(a.out + r0 * R, sm, (uint32_t)(runs * R * 16));
+            tensor_store_2d(&map, sb, 0, (int)(t * kTileRows));
             bulk_commit();
         }
         buf ^= 1;
@@ -209,10 +246,30 @@ __global__ void __launch_bounds__(256) fill_tyche_kernel(FillArgs a)
     }
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
+    return fn;
+}
+
+// Output rows per launch: tensor coordinates are signed 32-bit, so a fill
+// larger than 2^30 rows (128 GiB) is split into launches of whole rows.
+constexpr uint64_t kMaxRowsPerLaunch = 1ull << 30;
+
 template <int GEN, int DT, int R, int T, int TR>
 static orand_status_t launch_tile_shape(TileArgs a, const DeviceInfo &info, cudaStream_t stream)
 {
-    const size_t smem = 2u * (size_t)T * TR * R * sizeof(uint4);
+    constexpr uint32_t kTileRows = (uint32_t)T * TR * R * 16 / 128;
+    const size_t smem = 2u * (size_t)T * TR * R * sizeof(uint4) + 1024;
     static bool configured = false;  // per instantiation; idempotent, so a race is harmless
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(fill_tile_kernel<GEN, DT, R, T, TR>,
@@ -220,16 +277,44 @@ static orand_status_t launch_tile_shape(TileArgs a, const DeviceInfo &info, cuda
         if (e != cudaSuccess) return cuda_status(e);
         configured = true;
     }
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (encode == nullptr) return ORAND_ERR_CUDA;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_tile_kernel<GEN, DT, R, T, TR>, T,
                                                                   smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (per_sm < 1) per_sm = 1;
-    a.n_tiles = ceil_div(a.n_runs, (uint64_t)T * TR);
-    uint64_t grid = (uint64_t)per_sm * info.sm_count;
-    if (grid > a.n_tiles) grid = a.n_tiles;
-    fill_tile_kernel<GEN, DT, R, T, TR><<<(unsigned)grid, T, smem, stream>>>(a);
-    return launch_status();
+    const uint64_t total_runs = a.n_runs;
+    const uint64_t runs_per_launch = kMaxRowsPerLaunch * 8 / R;
+    uint4 *const out0 = a.out;
+    for (uint64_t r0 = 0; r0 < total_runs; r0 += runs_per_launch) {
+        TileArgs p = a;
+        p.r_first = r0;
+        // The last launch takes a remainder of less than one row as well, so
+        // every launch has at least one full row.
+        const uint64_t left = total_runs - r0;
+        p.n_runs = left <= runs_per_launch || left - runs_per_launch < 8 / R ? left : runs_per_launch;
+        p.out = out0 + r0 * R;
+        const uint64_t rows = p.n_runs * R / 8;  // >= 1: the caller sends at least 128 bytes here
+        p.full_chunks = rows * 8;
+        p.n_tiles = ceil_div(p.n_runs, (uint64_t)T * TR);
+        // 32 words x rows, 128-byte rows, box of one tile, 128-byte swizzle.
+        CUtensorMap map;
+        const cuuint64_t dims[2] = {32, rows};
+        const cuuint64_t strides[1] = {128};
+        const cuuint32_t box[2] = {32, kTileRows};
+        const cuuint32_t elem_strides[2] = {1, 1};
+        if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)p.out, dims, strides, box, elem_strides,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return ORAND_ERR_CUDA;
+        uint64_t grid = (uint64_t)per_sm * info.sm_count;
+        if (grid > p.n_tiles) grid = p.n_tiles;
+        fill_tile_kernel<GEN, DT, R, T, TR><<<(unsigned)grid, T, smem, stream>>>(map, p);
+        const orand_status_t st = launch_status();
+        if (st != ORAND_OK) return st;
+    }
+    return ORAND_OK;
 }
 
 template <int GEN, int DT, int R>
@@ -336,8 +421,9 @@ orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uin
     const uint32_t V = dt == ORAND_F64_UNIFORM ? 2u : 4u;
     const uint64_t G = ceil_div(dps, V);
     const bool vec16 = (dps % V == 0) && ((uintptr_t)out % 16 == 0);
-    // Tiled path: vector-aligned output; Tyche only when a whole stream fits a run.
-    if (vec16 && !(gen == ORAND_TYCHE && G > 8) && !tile_path_disabled()) {
+    // Tiled path: vector-aligned output of at least one 128-byte row; Tyche
+    // only when a whole stream fits a run.
+    if (vec16 && n_streams * G >= 8 && !(gen == ORAND_TYCHE && G > 8) && !tile_path_disabled()) {
         int R = 1;
         if (gen == ORAND_TYCHE) R = (int)G;
         else while (R < 8 && G % (2 * R) == 0) R *= 2;
@@ -347,7 +433,9 @@ orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uin
             t.counter = counter;
             t.rps = G / R;
             t.n_runs = n_streams * t.rps;
-            t.n_tiles = 0;  // set per launch shape
+            t.r_first = 0;
+            t.n_tiles = 0;      // set per launch
+            t.full_chunks = 0;  // set per launch
             t.rps_shift = (t.rps & (t.rps - 1)) == 0 ? __builtin_ctzll(t.rps) : -1;
             t.out = (uint4 *)out;
             switch (gen) {

@@ -53,7 +53,10 @@ def gpu_fill(torch, gen, dtype, seed, counter, n_streams, dps, offset_elems=0):
     return to_numpy(out)
 
 
-SHAPES = [(1, 1), (3, 5), (257, 4), (100, 16), (33, 67), (1000, 8), (5, 130), (77, 96), (300, 48), (513, 32)]
+# (7, 4): under one 128-byte row (untiled); (9, 4), (65, 8), (3, 40): full rows
+# plus a partial row; (2, 16): exactly one row; (3, 40): 5 runs per stream.
+SHAPES = [(1, 1), (3, 5), (257, 4), (100, 16), (33, 67), (1000, 8), (5, 130), (77, 96), (300, 48), (513, 32),
+          (7, 4), (9, 4), (2, 16), (65, 8), (3, 40)]
 
 
 @pytest.mark.parametrize("gen", GENS)
@@ -74,6 +77,18 @@ def test_fill_unaligned_output_takes_scalar_path(torch_cuda, orc, gen, dtype):
     ref = orc.fill(gen, dtype, 99, 3, 300, 16)
     got = gpu_fill(torch_cuda, gen, dtype, 99, 3, 300, 16, offset_elems=1)
     compare(dtype, got, ref)
+
+
+@pytest.mark.parametrize("gen", GENS)
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fill_output_off_row_boundary(torch_cuda, orc, gen, dtype):
+    # 16 bytes past an allocation's start: vector-aligned but not on a
+    # 128-byte row, so the tensor store's rows straddle the allocation's.
+    off = 2 if dtype == W.F64_UNIFORM else 4
+    for shape in [(300, 16), (1000, 8), (41, 32)]:
+        ref = orc.fill(gen, dtype, 1234, 5, *shape)
+        got = gpu_fill(torch_cuda, gen, dtype, 1234, 5, *shape, offset_elems=off)
+        compare(dtype, got, ref)
 
 
 @pytest.mark.parametrize("dtype", [W.U32, W.F32_UNIFORM])
