@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kCurandWalkBlock) walk2d_curand_step_kernel(ui
     states[i] = st;
 }
 
-__global__ void __launch_bounds__(kCurandWalkBlock) walk2d_curand_fused_kernel(uint64_t n, uint64_t p_first,
+__global__ void __launch_bounds__(kCurandWalkBlock, 1) walk2d_curand_fused_kernel(uint64_t n, uint64_t p_first,
                                                                               uint64_t seed, uint32_t steps, float s,
                                                                               float2 *__restrict__ pos)
 {
@@ -72,10 +72,17 @@ __global__ void __launch_bounds__(kCurandWalkBlock) walk2d_curand_fused_kernel(u
     for (uint32_t done = 0; done < steps;) {
         const uint32_t len = min(kCurandSumBlock, steps - done);
         float sx = 0.f, sy = 0.f;
-        for (uint32_t k = 0; k < len; ++k) {
+        auto step = [&]() {
             const float2 z = curand_normal2(&st);
             sx = fmaf(s, z.x, sx);
             sy = fmaf(s, z.y, sy);
+        };
+        if (len == kCurandSumBlock) {
+            // The same full-block unrolling and launch bounds as walk2d_kernel.
+#pragma unroll 4
+            for (uint32_t k = 0; k < kCurandSumBlock; ++k) step();
+        } else {
+            for (uint32_t k = 0; k < len; ++k) step();
         }
         kahan_add_cw(x, cx, sx);
         kahan_add_cw(y, cy, sy);
