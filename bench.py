@@ -45,9 +45,18 @@ ALU_PEAK = 148 * 128 * 2.032e9
 # folded (33), the walks' Box-Muller radius (19: u1 and v, the six-term
 # series, the log2 estimate, the selection and the square root) and angle
 # (19: quadrant reduction, sin and cos estimates, swap and signs), the step
-# scale, two FMA sums, the step loop shared by two particles and the Kahan
-# add of each 16-step block sum (5).
-WALK2D_OPS_PER_STEP = 76
+# scale and two FMA sums (3).  The Kahan add of each 16-step block sum and the
+# unrolled loop's control add under one per step.
+WALK2D_OPS_PER_STEP = 74
+# The same count per 3D particle-step, forward plus adjoint.  Forward: Philox
+# with all four words (35), two radii (38), one cos/sin pair (19), one cosine
+# (16: the same reduction, one sign), two radius scales, three products and
+# three sums (8) = 116; with the OU drift each sum is x + s, z + mu dt, an FMA
+# and the add (+9) = 125.  Adjoint: the same normals without the scales
+# (114); with the OU drift it also recomputes x, decays lambda and
+# accumulates dL/dmu, dL/dsigma and dL/dkappa (7 per component, +21) = 135.
+WALK3D_OPS_PER_STEP = 116 + 114
+WALK3D_OU_OPS_PER_STEP = 125 + 135
 
 
 def parse_args():
@@ -682,8 +691,9 @@ def main():
             e.update(r.finish())
         row_table[r.name] = e
 
-    # Per-kernel rooflines beside the headline: the step's dominant kernel
-    # (the 2D walk, issue-bound) against the issue peak.
+    # Per-kernel rooflines beside the headline: the step's dominant kernels
+    # (the 2D walk, and the 3D walks' forward + adjoint pairs; issue-bound)
+    # against the issue peak.
     rooflines = {}
     w2 = row_table.get("walk2d/fused")
     if w2:
@@ -692,6 +702,16 @@ def main():
                                       "frac": ops / ALU_PEAK, "ops_per_particle_step": WALK2D_OPS_PER_STEP,
                                       "share_of_step": w2["share_of_step"],
                                       "peak_kind": "derived: 148 SMs x 128 lanes x 2.032 GHz"}
+    for row, key, opc in [("walk3d/fused_fwd+adjoint", "walk3d_fwd_kernel<0>+walk3d_bwd_kernel<0>", WALK3D_OPS_PER_STEP),
+                          ("walk3d/ou_fused_fwd+adjoint", "walk3d_fwd_kernel<1>+walk3d_bwd_kernel<1>",
+                           WALK3D_OU_OPS_PER_STEP)]:
+        w3 = row_table.get(row)
+        if w3:
+            ops = w3["particle-steps_per_s"] / world * opc
+            rooflines[key] = {"bound": "alu", "achieved": ops, "peak": ALU_PEAK, "unit": "lane-ops/s",
+                              "frac": ops / ALU_PEAK, "ops_per_particle_step": opc,
+                              "share_of_step": w3["share_of_step"],
+                              "peak_kind": "derived: 148 SMs x 128 lanes x 2.032 GHz"}
     rooflines["fill_tile_kernel<philox,u32>"] = {"bound": "hbm", "frac": achieved / peak,
                                                  "share_of_step": row_table[head.name]["share_of_step"]}
 
