@@ -76,75 +76,53 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 
 // ------------------------------------------------------------------ 2D walk
 
-// The 2D kernel is bound by instruction issue (about 110 operations per
-// particle-step, nearly all of them the Philox rounds and Box-Muller).  Two
-// particles per thread give the schedulers two independent dependency
-// chains; the position sum is compensated per block of kSumBlock steps
-// (plain FMA sums inside a block, a Kahan add of each block sum), which
-// saves the per-step compensation while keeping the rounding error of the
-// whole walk at the level of one FP32 rounding per block sum.
-constexpr int kWalk2dBlock = 128;
-constexpr int kWalk2dPerThread = 2;
+// The 2D kernel is bound by instruction issue (74 operations per
+// particle-step, nearly all of them the Philox rounds and Box-Muller).  One
+// particle per thread; the position sum is compensated per block of
+// kSumBlock steps (plain FMA sums inside a block, a Kahan add of each block
+// sum), which saves the per-step compensation while keeping the rounding
+// error of the whole walk at the level of one FP32 rounding per block sum.
+// A full block runs a constant-trip-count loop unrolled by 4, which gives
+// the schedulers four steps' independent Philox chains; with the launch
+// bound of one block per SM, ptxas keeps the round keys in registers.
+// Measured on B300 (full walk): 470.5 ms, against 478.7 with two particles
+// per thread (108 registers) and 471-491 ms for three or four.
+constexpr int kWalk2dBlock = 256;
 constexpr uint32_t kSumBlock = 16;
 
-struct Walk2dLane {
-    orand::PhiloxKeys keys;
-    float x, y, cx, cy;
-    __device__ __forceinline__ explicit Walk2dLane(uint64_t key64) : keys(key64), cx(0.f), cy(0.f)
-    {
-        const uint4 w = keys.block(0u, 0u);
-        x = orand::u01_f32(w.x);
-        y = orand::u01_f32(w.y);
-    }
-};
-
-// Block b covers particles [b * 256, (b + 1) * 256): thread x owns x and x + 128.
 __global__ void __launch_bounds__(kWalk2dBlock, 1) walk2d_kernel(uint64_t n, uint64_t p_first, uint64_t seed,
-                                                             uint32_t steps, float s, float2 *__restrict__ out)
+                                                                uint32_t steps, float s, float2 *__restrict__ out)
 {
-    const uint64_t base = (uint64_t)blockIdx.x * (kWalk2dBlock * kWalk2dPerThread) + threadIdx.x;
-    Walk2dLane L[kWalk2dPerThread] = {Walk2dLane(seed ^ (p_first + base)),
-                                      Walk2dLane(seed ^ (p_first + base + kWalk2dBlock))};
+    const uint64_t i = (uint64_t)blockIdx.x * kWalk2dBlock + threadIdx.x;
+    if (i >= n) return;
+    const orand::PhiloxKeys keys(seed ^ (p_first + i));
+    const uint4 w0 = keys.block(0u, 0u);
+    float x = orand::u01_f32(w0.x), y = orand::u01_f32(w0.y), cx = 0.f, cy = 0.f;
     // t runs 1..steps in blocks of kSumBlock; `done` counts steps taken so
     // the loop cannot wrap when steps is near 2^32.
     for (uint32_t done = 0; done < steps;) {
         const uint32_t len = min(kSumBlock, steps - done);
-        float sx[kWalk2dPerThread] = {0.f, 0.f}, sy[kWalk2dPerThread] = {0.f, 0.f};
+        float sx = 0.f, sy = 0.f;
         auto step = [&](uint32_t t) {
-#pragma unroll
-            for (int j = 0; j < kWalk2dPerThread; ++j) {
-                const uint4 w = L[j].keys.block(0u, t);
-                // s * (r cos, r sin) with the step scale folded into the radius.
-                const float rs = s * orand::bm_radius_walk(w.x);
-                float c, sn;
-                orand::bm_cos_sin_walk(w.y, &c, &sn);
-                sx[j] = fmaf(rs, c, sx[j]);
-                sy[j] = fmaf(rs, sn, sy[j]);
-            }
+            const uint4 w = keys.block(0u, t);
+            // s * (r cos, r sin) with the step scale folded into the radius.
+            const float rs = s * orand::bm_radius_walk(w.x);
+            float c, sn;
+            orand::bm_cos_sin_walk(w.y, &c, &sn);
+            sx = fmaf(rs, c, sx);
+            sy = fmaf(rs, sn, sy);
         };
         if (len == kSumBlock) {
-            // A full block: the constant trip count lets the compiler unroll
-            // and interleave steps.  With the minimum of one block per SM in
-            // the launch bounds (so ptxas keeps the round keys in registers
-            // rather than recomputing them) this runs the full walk in 478
-            // instead of 500 ms on B300.
 #pragma unroll 4
             for (uint32_t k = 1; k <= kSumBlock; ++k) step(done + k);
         } else {
             for (uint32_t k = 1; k <= len; ++k) step(done + k);
         }
-#pragma unroll
-        for (int j = 0; j < kWalk2dPerThread; ++j) {
-            kahan_add(L[j].x, L[j].cx, sx[j]);
-            kahan_add(L[j].y, L[j].cy, sy[j]);
-        }
+        kahan_add(x, cx, sx);
+        kahan_add(y, cy, sy);
         done += len;
     }
-#pragma unroll
-    for (int j = 0; j < kWalk2dPerThread; ++j) {
-        const uint64_t i = base + (uint64_t)j * kWalk2dBlock;
-        if (i < n) out[i] = make_float2(L[j].x, L[j].y);
-    }
+    out[i] = make_float2(x, y);
 }
 
 // ------------------------------------------------------------------ 3D walk
@@ -674,7 +652,7 @@ orand_status_t orand_brownian_walk(const orand_walk2d_t *p, float *pos_out, cuda
     orand_status_t st = check_ptr(pos_out, 8);
     if (st != ORAND_OK) return st;
     if (p->steps == UINT32_MAX) return ORAND_ERR_OVERFLOW;  // counters 1..steps, same limit as the 3D walk
-    const uint64_t grid = ceil_div(p->n_particles, (uint64_t)kWalk2dBlock * kWalk2dPerThread);
+    const uint64_t grid = ceil_div(p->n_particles, (uint64_t)kWalk2dBlock);
     if (grid > 0x7FFFFFFFull) return ORAND_ERR_OVERFLOW;
     DeviceInfo info;
     if ((st = current_device(&info)) != ORAND_OK) return st;
