@@ -192,8 +192,12 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_init_kernel(Walk3dArgs a, f
 // is Kahan-added to the position, as in the 2D kernel.  OU: the drift
 // mu - kappa x is evaluated at the current position x + s (s the block's
 // partial sum); without it the constant drift mu dt is added once per block.
+// Launch bounds (measured on B300, forward + adjoint of 2^22 x 4096): one
+// block per SM for the constant drift (86 and 83 registers, 142.4 ms; three
+// blocks: 143.7 ms), three for OU (78 and 80 registers, 158.3 ms; one
+// block: 159.9 ms).
 template <bool OU>
-__global__ void __launch_bounds__(kWalkBlock, 1) walk3d_fwd_kernel(Walk3dArgs a, const float *__restrict__ x0_in,
+__global__ void __launch_bounds__(kWalkBlock, OU ? 3 : 1) walk3d_fwd_kernel(Walk3dArgs a, const float *__restrict__ x0_in,
                                                                float *__restrict__ xT, float *__restrict__ ckpt,
                                                                double *__restrict__ partials)
 {
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(kWalkBlock, 1) walk3d_fwd_kernel(Walk3dArgs a,
 //     in FP32 within a segment (at most K steps) and are re-anchored in FP64
 //     between segments.
 template <bool OU>
-__global__ void __launch_bounds__(kWalkBlock, 1) walk3d_bwd_kernel(Walk3dArgs a, const float *__restrict__ xT,
+__global__ void __launch_bounds__(kWalkBlock, OU ? 3 : 1) walk3d_bwd_kernel(Walk3dArgs a, const float *__restrict__ xT,
                                                                const float *__restrict__ ckpt,
                                                                const double *__restrict__ grad_loss,
                                                                float *__restrict__ dx0,
