@@ -158,3 +158,32 @@ def test_fill_large_workload_sampled(torch_cuda, orc, gen, dtype):
         assert abs(chi2 - 255) < 5 * math.sqrt(2 * 255)
     del out
     torch.cuda.empty_cache()
+
+
+def test_fill_over_2p30_rows_splits_launches(torch_cuda, orc):
+    """A u32 fill of 2^31 + 9 streams x 16 words (128 GiB + 576 B): more than
+    the 2^30 128-byte rows one tensor-store launch addresses, so the tiled
+    path runs a second launch of 9 streams, whose last 4 chunks form a
+    partial row.  Exact on the streams around the split and the end, and on
+    sampled streams."""
+    torch = torch_cuda
+    n_streams, dps, seed = (1 << 31) + 9, 16, 0x5EED
+    free, _ = torch.cuda.mem_get_info()
+    need = n_streams * dps * 4
+    if free < need + (8 << 30):
+        pytest.skip("needs %d GiB of free device memory" % ((need >> 30) + 8))
+    out = torch.empty(n_streams * dps + 4, dtype=torch.int32, device="cuda")
+    out[-4:] = -7
+    orand.fill(W.PHILOX, W.U32, seed, 0, n_streams, dps, out=out[:n_streams * dps])
+    torch.cuda.synchronize()
+    assert bool((out[-4:] == -7).all())
+    rng = np.random.default_rng(31)
+    streams = np.unique(np.concatenate([
+        [0, 1], np.arange((1 << 31) - 3, n_streams), rng.integers(0, n_streams, 64)]))
+    idx = torch.as_tensor((streams[:, None] * dps + np.arange(dps)[None, :]).ravel(), device="cuda")
+    got = to_numpy(out[idx]).reshape(len(streams), dps)
+    for i, s in enumerate(streams):
+        ref = orc.fill(W.PHILOX, W.U32, seed, 0, 1, dps, s_first=int(s))
+        assert np.array_equal(got[i], ref), int(s)
+    del out, idx
+    torch.cuda.empty_cache()
