@@ -562,6 +562,39 @@ def cpu_oracle_fill_rate(threads, n_streams=1 << 24, dps=16):
                                        "counter 0, on %d host threads" % (n_streams, dps, out.nbytes >> 20, threads))
 
 
+def cpu_oracle_row_rates(threads):
+    """The oracle on bounded samples of the other rows' workloads, for context
+    beside their GPU rates (a few seconds in all).  Walks step in FP64."""
+    import oracle
+    from paper_2310_19925_b300 import workloads as W
+
+    oracle.build()
+    rates = {}
+    n2, t2 = 1 << 14, W.WALK2D["steps"]
+    t0 = time.perf_counter()
+    oracle.walk2d(0, n2, t2, W.WALK2D["dt"], W.WALK2D["D"], threads=threads)
+    dt = time.perf_counter() - t0
+    rates["walk2d/fused"] = {"particle-steps_per_s": n2 * t2 / dt, "cores": threads,
+                             "sample": "%d particles x %d steps (FP64)" % (n2, t2)}
+    c3 = W.WALK3D
+    n3, t3 = 1 << 12, c3["steps"]
+    t0 = time.perf_counter()
+    xT, _ = oracle.walk3d_forward(0, n3, t3, c3["ckpt_every"], c3["dt"], c3["mu"], c3["sigma"], want_ckpt=True,
+                                  threads=threads)
+    oracle.walk3d_adjoint(0, n3, t3, c3["dt"], xT, c3["k"], float(n3), threads=threads)
+    dt = time.perf_counter() - t0
+    rates["walk3d/fused_fwd+adjoint"] = {"particle-steps_per_s": n3 * t3 / dt, "cores": threads,
+                                         "sample": "%d particles x %d steps, forward + adjoint (FP64)" % (n3, t3)}
+    recs, _ = W.ragged_requests()
+    sub = recs[:200]
+    t0 = time.perf_counter()
+    oracle.ragged(sub)
+    dt = time.perf_counter() - t0
+    rates["ragged/batched"] = {"values_per_s": int(sub["length"].sum()) / dt, "cores": 1,
+                               "sample": "the first 200 requests (%d values), one thread" % int(sub["length"].sum())}
+    return rates
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -769,6 +802,13 @@ def main():
         threads = os.cpu_count() or 1
         v, dt, sample = cpu_oracle_fill_rate(threads)
         cpu = {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample}
+        # The same oracle on samples of the walk and ragged rows, with the
+        # GPU row's rate over it (context: the oracle is deliberately plain).
+        cpu["rows"] = cpu_oracle_row_rates(threads)
+        for name, r in cpu["rows"].items():
+            unit = "particle-steps_per_s" if "particle-steps_per_s" in r else "values_per_s"
+            if name in row_table and unit in row_table[name]:
+                r["gpu_over_oracle"] = row_table[name][unit] / world / r[unit]
 
     if rank == 0:
         line = {

@@ -242,8 +242,18 @@ def fill(gen: int, dtype: int, seed: int, counter: int, n_streams: int, dps: int
 
 def ragged(requests) -> list:
     """Ragged batch: each request (gen, dtype, seed, counter, length) is the
-    single stream key64 = seed (stream id 0), i.e. fill(..., n_streams=1)."""
-    return [fill(r[0], r[1], r[2], r[3], 1, r[4]) for r in requests]
+    single stream key64 = seed (stream id 0), i.e. fill(..., n_streams=1).
+    A request is a 5-tuple in that order or a record with those field names
+    (the batcher's request layout has more fields)."""
+    out = []
+    for r in requests:
+        names = getattr(getattr(r, "dtype", None), "names", None)
+        if names:
+            g, d, s, c, n = (int(r[k]) for k in ("gen", "dtype", "seed", "counter", "length"))
+        else:
+            g, d, s, c, n = (int(x) for x in r[:5])
+        out.append(fill(g, d, s, c, 1, n))
+    return out
 
 
 # --- walks (§4 Fig. 1 structure; §5 macro-benchmark) -------------------------
