@@ -579,3 +579,17 @@ def test_ou_adjoint_vs_central_differences(orc):
     xm[2, 1] -= h
     fd = (loss(W3["mu"], W3["sigma"], kappa, xp) - loss(W3["mu"], W3["sigma"], kappa, xm)) / (2 * h)
     assert fd == pytest.approx(dx0[2, 1], rel=1e-7)
+
+
+def test_ragged_oracle_reads_request_records(orc):
+    """oracle.ragged takes the batcher's request records by field name (and
+    plain 5-tuples): each request is the single stream key64 = seed."""
+    from paper_2310_19925_b300 import workloads as W
+
+    recs, _ = W.ragged_requests(12, 6)
+    got = orc.ragged(recs)
+    tup = orc.ragged([(int(r["gen"]), int(r["dtype"]), int(r["seed"]), int(r["counter"]), int(r["length"]))
+                      for r in recs])
+    for r, a, b in zip(recs, got, tup):
+        ref = orc.fill(int(r["gen"]), int(r["dtype"]), int(r["seed"]), int(r["counter"]), 1, int(r["length"]))
+        assert len(a) == int(r["length"]) and np.array_equal(a, ref) and np.array_equal(b, ref)
