@@ -9,6 +9,7 @@
 // the vectorised path consecutive threads own consecutive groups, so every
 // warp store is one fully coalesced 512-byte row; the grid is sized to the
 // resident capacity of the 148 SMs and strides over the groups.
+#include <atomic>
 #include <cstdlib>
 
 #include <cuda.h>
@@ -270,12 +271,16 @@ static orand_status_t launch_tile_shape(TileArgs a, const DeviceInfo &info, cuda
 {
     constexpr uint32_t kTileRows = (uint32_t)T * TR * R * 16 / 128;
     const size_t smem = 2u * (size_t)T * TR * R * sizeof(uint4) + 1024;
-    static bool configured = false;  // per instantiation; idempotent, so a race is harmless
-    if (!configured) {
+    // The shared-memory opt-in is per device: one bit per ordinal (the call is
+    // idempotent, so a race only repeats it).  Ordinals past 63 set it on
+    // every launch.
+    static std::atomic<uint64_t> configured{0};
+    const uint64_t bit = info.device < 64 ? 1ull << info.device : 0;
+    if (bit == 0 || !(configured.load(std::memory_order_relaxed) & bit)) {
         cudaError_t e = cudaFuncSetAttribute(fill_tile_kernel<GEN, DT, R, T, TR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
-        configured = true;
+        configured.fetch_or(bit, std::memory_order_relaxed);
     }
     const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (encode == nullptr) return ORAND_ERR_CUDA;
