@@ -5,6 +5,7 @@
     python -m paper_2310_19925_b300.cases walk3d --particles 1048576 --steps 512
     python -m paper_2310_19925_b300.cases ragged --requests 2000 --max-log2 20
     python -m paper_2310_19925_b300.cases tyche-chain --dtype 3 --length 1048576
+    python -m paper_2310_19925_b300.cases langevin --form fused --particles 1000000 --steps 100
 
 Each case launches its kernels `--reps` times on the current stream.  Every
 launch is timed with CUDA events, and one line per case is printed with the
@@ -43,7 +44,7 @@ def timed(torch, fn, reps, busy_ms=0.0):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fill", "walk2d", "walk3d", "ragged", "tyche-chain"])
+    ap.add_argument("case", choices=["fill", "walk2d", "walk3d", "ragged", "tyche-chain", "langevin"])
     ap.add_argument("--gen", type=int, default=0)
     ap.add_argument("--dtype", type=int, default=0)
     ap.add_argument("--streams", type=int, default=1 << 24)
@@ -54,6 +55,8 @@ def main(argv=None):
     ap.add_argument("--max-log2", type=int, default=20)
     ap.add_argument("--length", type=int, default=1 << 20)
     ap.add_argument("--kappa", type=float, default=0.0, help="walk3d: OU drift mu - kappa x")
+    ap.add_argument("--form", choices=["fused", "per-step", "curand"], default="fused",
+                    help="langevin: the fused kernel, Fig. 1's launch per step, or Fig. 2's cuRAND pattern")
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args(argv)
 
@@ -95,6 +98,22 @@ def main(argv=None):
 
         ts = timed(torch, fn, args.reps)
         res.update(particles=args.particles, steps=args.steps, kappa=args.kappa, ms=statistics.mean(ts),
+                   particle_steps_per_s=args.particles * args.steps / (statistics.mean(ts) * 1e-3))
+    elif args.case == "langevin":
+        # The paper's macro-benchmark (FP64 Brownian dynamics); setup is untimed.
+        prm = orand.langevin2d_params(args.particles)
+        ps = orand.particles_tensor(args.particles)
+        st = torch.empty(args.particles * orand.orand_langevin2d_curand_state_bytes(), dtype=torch.uint8,
+                         device="cuda")
+        if args.form == "curand":
+            orand.orand_langevin2d_curand_setup(prm, ps.data_ptr(), st.data_ptr(), 1984, sh)
+            fn = lambda: orand.orand_langevin2d_curand_run(prm, ps.data_ptr(), st.data_ptr(), args.steps, sh)
+        else:
+            orand.orand_langevin2d_init(prm, ps.data_ptr(), sh)
+            run = orand.orand_langevin2d_fused if args.form == "fused" else orand.orand_langevin2d_run_per_step
+            fn = lambda: run(prm, ps.data_ptr(), 1, args.steps, sh)
+        ts = timed(torch, fn, args.reps)
+        res.update(form=args.form, particles=args.particles, steps=args.steps, ms=statistics.mean(ts),
                    particle_steps_per_s=args.particles * args.steps / (statistics.mean(ts) * 1e-3))
     elif args.case in ("ragged", "tyche-chain"):
         if args.case == "ragged":
