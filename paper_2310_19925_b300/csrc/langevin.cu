@@ -37,14 +37,35 @@ __device__ __forceinline__ double2 draw_double2(const orand::PhiloxKeys &keys, u
     return make_double2(orand::u01_f64(w.x, w.y), orand::u01_f64(w.z, w.w));
 }
 
-// One step of Fig. 1 with kick r: drag, kick, then the position update.
-__device__ __forceinline__ void langevin_update(const LangevinArgs &a, double2 r, double &x, double &y, double &vx,
-                                                double &vy)
+// 2r - 1 for the FP64 uniform r = u01_f64(hi, lo), built from integer bits.
+// With m = (hi:lo) >> 11 (53 bits), r = m 2^-53 and 2r - 1 = (m - 2^52) 2^-52,
+// which is exactly representable; Fig. 1's (r * 2 - 1) rounds to the same
+// value (both of its steps are exact), so this costs no FP64 operation and
+// changes no bit.
+__device__ __forceinline__ double u11_f64(uint32_t hi, uint32_t lo)
+{
+    const uint64_t m = (((uint64_t)hi << 32) | lo) >> 11;
+    const bool pos = (m >> 52) != 0;
+    const uint64_t a = pos ? (m & ((1ull << 52) - 1)) : (1ull << 52) - m;  // |m - 2^52| <= 2^52
+    if (a == 0) return 0.0;                                                 // 1.0 - 1.0 = +0
+    const int lz = __clzll((long long)a);                                   // 11..63
+    const uint64_t mant = (a << (lz - 11)) & ((1ull << 52) - 1);            // leading bit dropped
+    const uint64_t bits = ((uint64_t)!pos << 63) | ((uint64_t)(1034 - lz) << 52) | mant;  // 2^(11 - lz)
+    return __longlong_as_double((long long)bits);
+}
+
+// One step of Fig. 1 (drag, kick, then the position update) with the kicks'
+// 2r - 1 taken from the block's words by u11_f64: 14 FP64 operations instead
+// of Fig. 1's 18, the same bits.  The FP64 pipe
+// bounds this simulation on B300, so the fused kernel uses this form; the
+// per-step kernel keeps Fig. 1's arithmetic.
+__device__ __forceinline__ void langevin_update_words(const LangevinArgs &a, uint4 w, double &x, double &y,
+                                                      double &vx, double &vy)
 {
     vx = __dsub_rn(vx, __dmul_rn(__dmul_rn(a.g_over_m, vx), a.dt));
     vy = __dsub_rn(vy, __dmul_rn(__dmul_rn(a.g_over_m, vy), a.dt));
-    vx = __dadd_rn(vx, __dmul_rn(__dsub_rn(__dmul_rn(r.x, 2.0), 1.0), a.sqrt_dt));
-    vy = __dadd_rn(vy, __dmul_rn(__dsub_rn(__dmul_rn(r.y, 2.0), 1.0), a.sqrt_dt));
+    vx = __dadd_rn(vx, __dmul_rn(u11_f64(w.x, w.y), a.sqrt_dt));
+    vy = __dadd_rn(vy, __dmul_rn(u11_f64(w.z, w.w), a.sqrt_dt));
     x = __dadd_rn(x, __dmul_rn(vx, a.dt));
     y = __dadd_rn(y, __dmul_rn(vy, a.dt));
 }
@@ -94,7 +115,7 @@ __global__ void __launch_bounds__(kLangevinBlock) langevin_fused_kernel(Langevin
     orand_particle_t p = ps[i];
     const orand::PhiloxKeys keys(a.seed ^ p.pid);
     double x = p.x, y = p.y, vx = p.vx, vy = p.vy;
-    for (uint32_t k = 0; k < steps; ++k) langevin_update(a, draw_double2(keys, first_counter + k), x, y, vx, vy);
+    for (uint32_t k = 0; k < steps; ++k) langevin_update_words(a, keys.block(0u, first_counter + k), x, y, vx, vy);
     p.x = x;
     p.y = y;
     p.vx = vx;
