@@ -32,9 +32,13 @@ def torch_cuda():
     return torch
 
 
-def pos_close(gpu, ref):
+def pos_close(gpu, ref, scale=1.0):
+    """|gpu - ref| <= POS_TOL * max(|ref|, scale): relative, with the floor at
+    the walk's own length scale (1 for the benchmark walks, whose steps are
+    below it; s sqrt(steps) for walks of larger steps, where positions that
+    end near 0 are sums that cancelled)."""
     err = np.abs(gpu.astype(np.float64) - ref)
-    bound = POS_TOL * np.maximum(np.abs(ref), 1.0)
+    bound = POS_TOL * np.maximum(np.abs(ref), scale)
     assert np.all(err <= bound), "worst %.3g (bound %.3g)" % ((err / bound).max(), POS_TOL)
 
 
@@ -50,6 +54,16 @@ def test_walk2d_small(torch_cuda, orc, steps, p_first):
     if steps == 0:
         assert np.array_equal(got.astype(np.float64), x0)
     pos_close(got, xT)
+
+
+@pytest.mark.parametrize("D,dt", [(1e30, 1.0), (1e-32, 1.0)])
+def test_walk2d_extreme_step_scales(torch_cuda, orc, D, dt):
+    # Step scales s = sqrt(2 D dt) of about 1.4e15 and 1.4e-16.
+    n, steps = 1000, 37
+    got = to_numpy(orand.brownian_walk(n, steps, dt=dt, D=D, seed=0x77))
+    x0, xT = orc.walk2d(0x77, n, steps, _f32(dt), _f32(D), threads=8)
+    s = float(np.float32(np.sqrt(2.0 * _f32(D) * _f32(dt))))
+    pos_close(got, xT, scale=max(1.0, s * np.sqrt(steps)))
 
 
 def test_walk2d_full_workload_sampled(torch_cuda, orc):
@@ -81,6 +95,18 @@ def _p(n, steps, K=16, p_first=0, p_total=0, seed=0, mu=MU, sigma=0.5):
 
 def _f32(v):
     return float(np.float32(v))
+
+
+def test_walk3d_forward_extreme_noise_scale(torch_cuda, orc):
+    # sigma sqrt(dt) of about 3.2e14.
+    n, steps, K, sigma = 300, 65, 16, 1e16
+    p = _p(n, steps, K, sigma=sigma)
+    xT, ck, loss = orand.walk3d_forward(p)
+    torch_cuda.cuda.synchronize()
+    oxT, ock = orc.walk3d_forward(0, n, steps, K, _f32(1e-3), MU, _f32(sigma), want_ckpt=True)
+    scale = _f32(sigma) * np.sqrt(_f32(1e-3) * steps)
+    pos_close(to_numpy(xT), oxT, scale=scale)
+    pos_close(to_numpy(ck), ock, scale=scale)
 
 
 @pytest.mark.parametrize("n,steps,K", [(1, 1, 1), (777, 200, 16), (300, 65, 64), (513, 0, 8)])
