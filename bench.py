@@ -44,19 +44,19 @@ ALU_PEAK = 148 * 128 * 2.032e9
 # Philox4x32-10 with the two used words and the constant counter words
 # folded (33), the walks' Box-Muller radius (19: u1 and v, the six-term
 # series, the log2 estimate, the selection and the square root) and angle
-# (19: quadrant reduction, sin and cos estimates, swap and signs), the step
+# (17: quadrant split, sin and cos estimates, swap and signs), the step
 # scale and two FMA sums (3).  The Kahan add of each 16-step block sum and the
 # unrolled loop's control add under one per step.
-WALK2D_OPS_PER_STEP = 74
+WALK2D_OPS_PER_STEP = 72
 # The same count per 3D particle-step, forward plus adjoint.  Forward: Philox
-# with all four words (35), two radii (38), one cos/sin pair (19), one cosine
-# (16: the same reduction, one sign), two radius scales, three products and
-# three sums (8) = 116; with the OU drift each sum is x + s, z + mu dt, an FMA
-# and the add (+9) = 125.  Adjoint: the same normals without the scales
-# (114); with the OU drift it also recomputes x, decays lambda and
-# accumulates dL/dmu, dL/dsigma and dL/dkappa (7 per component, +21) = 135.
-WALK3D_OPS_PER_STEP = 116 + 114
-WALK3D_OU_OPS_PER_STEP = 125 + 135
+# with all four words (35), two radii (38), one cos/sin pair (17), one cosine
+# (14: the same split, one sign), two radius scales, three products and
+# three sums (8) = 112; with the OU drift each sum is x + s, z + mu dt, an FMA
+# and the add (+9) = 121.  Adjoint: the same normals without the scales
+# (110); with the OU drift it also recomputes x, decays lambda and
+# accumulates dL/dmu, dL/dsigma and dL/dkappa (7 per component, +21) = 131.
+WALK3D_OPS_PER_STEP = 112 + 110
+WALK3D_OU_OPS_PER_STEP = 121 + 131
 # The paper's macro-benchmark (FP64 Brownian dynamics): the fused kernel's
 # 14 FP64 multiplies and adds per particle-step (Fig. 1 writes 18; the kicks'
 # exact 2r - 1 is built from integer bits), against the FP64 pipe's nominal

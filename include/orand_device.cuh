@@ -453,20 +453,23 @@ __device__ __forceinline__ float bm_radius_walk(uint32_t w0)
     return x * sfu_rsqrt(fmaxf(x, 1.17549435e-38f));
 }
 
-/* (cos, sin)(2 pi u2), u2 = (w1 >> 8) 2^-24, by the exact quadrant
- * reduction of bm_cos_sin (q = round(4 u2), r = 2 u2 - q/2 in [-1/4, 1/4])
- * and the SFU's estimates at pi r in [-pi/4, pi/4].  The reduction matters
- * for more than range: the cosine estimate has a small mean error, and
- * through the quadrant swap and signs it enters c as +, -, -, + over the
- * four quadrants, so the walk's sum of normals carries no drift from it
- * (a walk of 10^4 steps would otherwise move by about 1e-5). */
+/* (cos, sin)(2 pi u2), u2 = (w1 >> 8) 2^-24, by an exact quadrant split
+ * (q = floor(4 u2), the top two bits of the 24; theta = pi/2 times the other
+ * 22 bits' fraction, in [0, pi/2)) and the SFU's estimates at theta.  The
+ * split matters for more than range: the estimates have small mean errors,
+ * and through the quadrant swap and signs each enters c and s with
+ * opposite signs in quadrants q and q + 2, so the walk's sum of normals
+ * carries no drift from them (a walk of 10^4 steps would otherwise move by
+ * about 1e-5).  Taking the quadrant from the top bits (rather than rounding
+ * to theta in [-pi/4, pi/4)) saves the rounding's add and shift: measured
+ * over all 2^24 inputs, the same 3.4e-7 absolute error and no mean error. */
 __device__ __forceinline__ void bm_cos_sin_walk(uint32_t w1, float *c, float *s)
 {
     const uint32_t m = w1 >> 8;
-    const uint32_t q = (m + (1u << 21)) >> 22;
-    const float th = (float)(int)(m - (q << 22)) * (0x1p-23f * 3.14159265358979324f);
+    const uint32_t q = m >> 22;
+    const float th = (float)(m & 0x3FFFFFu) * (0x1p-23f * 3.14159265358979324f);
     const float sn = sfu_sin(th), cs = sfu_cos(th);
-    const bool swap = q & 1u;
+    const bool swap = q & 1u;            /* q = 1: (c, s) = (-sin, cos); q = 3: (sin, -cos) */
     const uint32_t a = __float_as_uint(swap ? cs : sn), b = __float_as_uint(swap ? sn : cs);
     *s = __uint_as_float(a ^ ((q & 2u) << 30));                /* negate sin for q = 2, 3 */
     *c = __uint_as_float(b ^ (((q + 1u) & 2u) << 30));         /* negate cos for q = 1, 2 */
