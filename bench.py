@@ -42,22 +42,22 @@ METRIC = "Philox u32 fill GB/s vs HBM peak; walk particle-steps/s; adjoint vs pl
 ALU_PEAK = 148 * 128 * 2.032e9
 # Algorithmic operations per 2D particle-step, counted from the kernel source:
 # Philox4x32-10 with the two used words and the constant counter words
-# folded (33), the walks' Box-Muller radius (18: u1 and v, the six-term
+# folded (33), the walks' Box-Muller radius (16: u1 and v, the six-term
 # series with its factor 2 folded in, the log2 estimate, the selection and
-# the square root) and angle
+# the square-root estimate) and angle
 # (17: quadrant split, sin and cos estimates, swap and signs), the step
 # scale and two FMA sums (3).  The Kahan add of each 16-step block sum and the
 # unrolled loop's control add under one per step.
-WALK2D_OPS_PER_STEP = 71
+WALK2D_OPS_PER_STEP = 69
 # The same count per 3D particle-step, forward plus adjoint.  Forward: Philox
-# with all four words (35), two radii (36), one cos/sin pair (17), one cosine
+# with all four words (35), two radii (32), one cos/sin pair (17), one cosine
 # (14: the same split, one sign), two radius scales, three products and
-# three sums (8) = 110; with the OU drift each sum is x + s, z + mu dt, an FMA
-# and the add (+9) = 119.  Adjoint: the same normals without the scales
-# (108); with the OU drift it also recomputes x, decays lambda and
-# accumulates dL/dmu, dL/dsigma and dL/dkappa (7 per component, +21) = 129.
-WALK3D_OPS_PER_STEP = 110 + 108
-WALK3D_OU_OPS_PER_STEP = 119 + 129
+# three sums (8) = 106; with the OU drift each sum is x + s, z + mu dt, an FMA
+# and the add (+9) = 115.  Adjoint: the same normals without the scales
+# (104); with the OU drift it also recomputes x, decays lambda and
+# accumulates dL/dmu, dL/dsigma and dL/dkappa (7 per component, +21) = 125.
+WALK3D_OPS_PER_STEP = 106 + 104
+WALK3D_OU_OPS_PER_STEP = 115 + 125
 # The paper's macro-benchmark (FP64 Brownian dynamics): the fused kernel's
 # 14 FP64 multiplies and adds per particle-step (Fig. 1 writes 18; the kicks'
 # exact 2r - 1 is built from integer bits), against the FP64 pipe's nominal
