@@ -45,19 +45,20 @@ ALU_PEAK = 148 * 128 * 2.032e9
 # folded (33), the walks' Box-Muller radius (16: u1 and v, the six-term
 # series with its factor 2 folded in, the log2 estimate, the selection and
 # the square-root estimate) and angle
-# (17: quadrant split, sin and cos estimates, swap and signs), the step
-# scale and two FMA sums (3).  The Kahan add of each 16-step block sum and the
+# (11: the 22 angle bits masked, converted and scaled, sin and cos
+# estimates, swap and signs from w1's top two bits), the step scale and two
+# FMA sums (3).  The Kahan add of each 16-step block sum and the
 # unrolled loop's control add under one per step.
-WALK2D_OPS_PER_STEP = 69
+WALK2D_OPS_PER_STEP = 63
 # The same count per 3D particle-step, forward plus adjoint.  Forward: Philox
-# with all four words (35), two radii (32), one cos/sin pair (17), one cosine
-# (14: the same split, one sign), two radius scales, three products and
-# three sums (8) = 106; with the OU drift each sum is x + s, z + mu dt, an FMA
-# and the add (+9) = 115.  Adjoint: the same normals without the scales
-# (104); with the OU drift it also recomputes x, decays lambda and
-# accumulates dL/dmu, dL/dsigma and dL/dkappa (7 per component, +21) = 125.
-WALK3D_OPS_PER_STEP = 106 + 104
-WALK3D_OU_OPS_PER_STEP = 115 + 125
+# with all four words (35), two radii (32), one cos/sin pair (11), one cosine
+# (9: the same split, one select and sign), two radius scales, three products
+# and three sums (8) = 95; with the OU drift each sum is x + s, z + mu dt, an
+# FMA and the add (+9) = 104.  Adjoint: the same normals without the scales
+# (93); with the OU drift it also recomputes x, decays lambda and
+# accumulates dL/dmu, dL/dsigma and dL/dkappa (7 per component, +21) = 114.
+WALK3D_OPS_PER_STEP = 95 + 93
+WALK3D_OU_OPS_PER_STEP = 104 + 114
 # The paper's macro-benchmark (FP64 Brownian dynamics): the fused kernel's
 # 14 FP64 multiplies and adds per particle-step (Fig. 1 writes 18; the kicks'
 # exact 2r - 1 is built from integer bits), against the FP64 pipe's nominal
