@@ -40,25 +40,23 @@ METRIC = "Philox u32 fill GB/s vs HBM peak; walk particle-steps/s; adjoint vs pl
 # Issue peak of the integer/FP32 pipes: 148 SMs x 4 schedulers x 32 lanes x
 # 2.032 GHz (the B300's unit counts and maximum SM clock), in lane-operations/s.
 ALU_PEAK = 148 * 128 * 2.032e9
-# Algorithmic operations per 2D particle-step, counted from the kernel source:
-# Philox4x32-10 with the two used words and the constant counter words
-# folded (33), the walks' Box-Muller radius (16: u1 and v, the six-term
-# series with its factor 2 folded in, the log2 estimate, the selection and
-# the square-root estimate) and angle
-# (11: the 22 angle bits masked, converted and scaled, sin and cos
-# estimates, swap and signs from w1's top two bits), the step scale and two
-# FMA sums (3).  The Kahan add of each 16-step block sum and the
-# unrolled loop's control add under one per step.
-WALK2D_OPS_PER_STEP = 63
-# The same count per 3D particle-step, forward plus adjoint.  Forward: Philox
-# with all four words (35), two radii (32), one cos/sin pair (11), one cosine
-# (9: the same split, one select and sign), two radius scales, three products
-# and three sums (8) = 95; with the OU drift each sum is x + s, z + mu dt, an
-# FMA and the add (+9) = 104.  Adjoint: the same normals without the scales
-# (93); with the OU drift it also recomputes x, decays lambda and
-# accumulates dL/dmu, dL/dsigma and dL/dkappa (7 per component, +21) = 114.
-WALK3D_OPS_PER_STEP = 95 + 93
-WALK3D_OU_OPS_PER_STEP = 104 + 114
+# Operations per 2D particle-step: the lane-instructions the kernel's source
+# needs per step, confirmed by ncu (68.1 at 2^20 x 1000): Philox4x32-10 with
+# the two used words and the constant counter words folded (33), the walks'
+# Box-Muller radius (u1 and v, the six-term series with its factor 2 folded
+# in, the log2 and square-root estimates, the selection) and angle (the 22
+# angle bits masked, converted and scaled, the sin and cos estimates with the
+# multiply the compiler puts before them, swap and signs from w1's top bits)
+# about 30 together, the step scale and two FMA sums (3), and the Kahan add
+# of each 16-step block sum and the unrolled loop's control (2).
+WALK2D_OPS_PER_STEP = 68
+# The same per 3D particle-step, forward plus adjoint (ncu: 103.9 + 101.5;
+# with the OU drift 112.6 + 123.3): Philox with all four words, two radii, a
+# cos/sin pair and a cosine, the scales, products and sums; the OU forward
+# adds the drift at the current position, the OU adjoint the recompute of x,
+# the lambda decay and the three gradient sums.
+WALK3D_OPS_PER_STEP = 104 + 101
+WALK3D_OU_OPS_PER_STEP = 113 + 123
 # The paper's macro-benchmark (FP64 Brownian dynamics): the fused kernel's
 # 14 FP64 multiplies and adds per particle-step (Fig. 1 writes 18; the kicks'
 # exact 2r - 1 is built from integer bits), against the FP64 pipe's nominal
