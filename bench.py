@@ -50,12 +50,13 @@ ALU_PEAK = 148 * 128 * 2.032e9
 # about 30 together, the step scale and two FMA sums (3), and the Kahan add
 # of each 16-step block sum and the unrolled loop's control (2).
 WALK2D_OPS_PER_STEP = 68
-# The same per 3D particle-step, forward plus adjoint (ncu: 103.9 + 101.5;
+# The same per 3D particle-step, forward plus adjoint (ncu: 101.9 + 101.5;
 # with the OU drift 112.6 + 123.3): Philox with all four words, two radii, a
-# cos/sin pair and a cosine, the scales, products and sums; the OU forward
-# adds the drift at the current position, the OU adjoint the recompute of x,
-# the lambda decay and the three gradient sums.
-WALK3D_OPS_PER_STEP = 104 + 101
+# cos/sin pair and a cosine, the products and sums (the constant-drift
+# forward scales each block sum once; the OU forward scales every step); the
+# OU forward adds the drift at the current position, the OU adjoint the
+# recompute of x, the lambda decay and the three gradient sums.
+WALK3D_OPS_PER_STEP = 102 + 101
 WALK3D_OU_OPS_PER_STEP = 113 + 123
 # The paper's macro-benchmark (FP64 Brownian dynamics): the fused kernel's
 # 14 FP64 multiplies and adds per particle-step (Fig. 1 writes 18; the kicks'

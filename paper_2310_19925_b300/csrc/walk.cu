@@ -227,9 +227,12 @@ __global__ void __launch_bounds__(kWalkBlock, OU ? 3 : 1) walk3d_fwd_kernel(Walk
             uint32_t len = min(kSumBlock, a.steps - t);
             if (want_ck) len = min(len, next_ck - t);
             float sum[3] = {0.f, 0.f, 0.f};
+            // OU: the drift needs each scaled step.  Constant drift: the block
+            // sums the unit normals and scales the sum once at the flush.
             auto step = [&](uint32_t tc) {
                 float z[3];
-                walk3d_scaled_normals(keys, tc, a.sig_sqdt, z);
+                if (OU) walk3d_scaled_normals(keys, tc, a.sig_sqdt, z);
+                else walk3d_normals(keys, tc, z);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     if (OU) sum[q] += fmaf(-a.kappa_dt, x[q] + sum[q], z[q] + a.mu_dt[q]);
@@ -244,7 +247,8 @@ __global__ void __launch_bounds__(kWalkBlock, OU ? 3 : 1) walk3d_fwd_kernel(Walk
                 for (uint32_t k = 0; k < len; ++k) step(t + k + 1u);
             }
 #pragma unroll
-            for (int q = 0; q < 3; ++q) kahan_add(x[q], c[q], OU ? sum[q] : fmaf((float)len, a.mu_dt[q], sum[q]));
+            for (int q = 0; q < 3; ++q)
+                kahan_add(x[q], c[q], OU ? sum[q] : fmaf((float)len, a.mu_dt[q], a.sig_sqdt * sum[q]));
             t += len;
         }
         xT[3 * i] = x[0];
