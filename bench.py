@@ -41,17 +41,18 @@ METRIC = "Philox u32 fill GB/s vs HBM peak; walk particle-steps/s; adjoint vs pl
 # 2.032 GHz (the B300's unit counts and maximum SM clock), in lane-operations/s.
 ALU_PEAK = 148 * 128 * 2.032e9
 # Operations per 2D particle-step: the lane-instructions the kernel's source
-# needs per step, confirmed by ncu (68.1 at 2^20 x 1000): Philox4x32-10 with
+# needs per step, confirmed by ncu (at 2^20 x 1000): Philox4x32-10 with
 # the two used words and the constant counter words folded (33), the walks'
 # Box-Muller radius (u1 and v, the six-term series with its factor 2 folded
 # in, the log2 and square-root estimates, the selection) and angle (the 22
 # angle bits masked, converted and scaled, the sin and cos estimates with the
 # multiply the compiler puts before them, swap and signs from w1's top bits)
-# about 30 together, the step scale and two FMA sums (3), and the Kahan add
-# of each 16-step block sum and the unrolled loop's control (2).
-WALK2D_OPS_PER_STEP = 68
-# The same per 3D particle-step, forward plus adjoint (ncu: 101.9 + 101.5;
-# with the OU drift 112.6 + 123.3): Philox with all four words, two radii, a
+# about 30 together, two FMA sums (2; the block sum is scaled by s once),
+# and the Kahan add of each 16-step block sum and the unrolled loop's
+# control (2).
+WALK2D_OPS_PER_STEP = 67
+# The same per 3D particle-step, forward plus adjoint (ncu-confirmed;
+# with the OU drift 112.6 + 123.3 by ncu): Philox with all four words, two radii, a
 # cos/sin pair and a cosine, the products and sums (the constant-drift
 # forward scales each block sum once; the OU forward scales every step); the
 # OU forward adds the drift at the current position, the OU adjoint the

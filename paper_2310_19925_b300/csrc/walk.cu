@@ -105,12 +105,12 @@ __global__ void __launch_bounds__(kWalk2dBlock, 1) walk2d_kernel(uint64_t n, uin
         float sx = 0.f, sy = 0.f;
         auto step = [&](uint32_t t) {
             const uint4 w = keys.block(0u, t);
-            // s * (r cos, r sin) with the step scale folded into the radius.
-            const float rs = s * orand::bm_radius_walk(w.x);
+            // (r cos, r sin); the block sum is scaled by s once, at the flush.
+            const float r = orand::bm_radius_walk(w.x);
             float c, sn;
             orand::bm_cos_sin_walk(w.y, &c, &sn);
-            sx = fmaf(rs, c, sx);
-            sy = fmaf(rs, sn, sy);
+            sx = fmaf(r, c, sx);
+            sy = fmaf(r, sn, sy);
         };
         if (len == kSumBlock) {
 #pragma unroll 4
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(kWalk2dBlock, 1) walk2d_kernel(uint64_t n, uin
         } else {
             for (uint32_t k = 1; k <= len; ++k) step(done + k);
         }
-        kahan_add(x, cx, sx);
-        kahan_add(y, cy, sy);
+        kahan_add(x, cx, s * sx);
+        kahan_add(y, cy, s * sy);
         done += len;
     }
     out[i] = make_float2(x, y);
