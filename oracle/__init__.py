@@ -138,7 +138,8 @@ def squares32(ctr: int, key: int) -> int:
 
 
 def squares_key(key64: int) -> int:
-    """Per-stream Squares key: fmix64(key64) | 1 (this build's reading)."""
+    """Per-stream Squares key: fmix64(key64) | 1 (a reading: the paper's
+    library takes 32-bit seeds for Squares)."""
     return int(lib().orc_squares_key(key64 & (2**64 - 1)))
 
 

@@ -140,8 +140,8 @@ uint32_t orc_squares32(uint64_t ctr, uint64_t key)
 }
 
 /* Squares takes one 64-bit key per stream.  The paper's library accepts
- * 32-bit seeds for Squares (§3, footnote); this build's reading derives the
- * key from the 64-bit stream key with the published MurmurHash3 64-bit
+ * 32-bit seeds for Squares (§3, footnote); the reading taken here derives
+ * the key from the 64-bit stream key with the published MurmurHash3 64-bit
  * finaliser (Appleby) and forces it odd: key = fmix64(key64) | 1. */
 uint64_t orc_squares_key(uint64_t key64)
 {
