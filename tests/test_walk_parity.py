@@ -109,7 +109,7 @@ def test_walk3d_forward_extreme_noise_scale(torch_cuda, orc):
     pos_close(to_numpy(ck), ock, scale=scale)
 
 
-@pytest.mark.parametrize("n,steps,K", [(1, 1, 1), (777, 200, 16), (300, 65, 64), (513, 0, 8)])
+@pytest.mark.parametrize("n,steps,K", [(1, 1, 1), (777, 200, 16), (300, 65, 64), (513, 0, 8), (400, 130, 24)])
 def test_walk3d_forward_small(torch_cuda, orc, n, steps, K):
     p = _p(n, steps, K, p_first=3)
     x0 = orand.walk3d_init(p)
@@ -261,7 +261,8 @@ def _pou(n, steps, K, kappa, p_first=0, p_total=0, seed=0):
 
 
 @pytest.mark.parametrize("n,steps,K,kappa", [(777, 200, 16, 1.5), (300, 203, 16, 1.5), (513, 97, 8, 20.0),
-                                             (129, 64, 64, -3.0), (1, 1, 1, 0.5), (256, 150, 32, 0.0)])
+                                             (129, 64, 64, -3.0), (1, 1, 1, 0.5), (256, 150, 32, 0.0),
+                                             (400, 130, 24, 1.5)])
 def test_walk3d_ou_forward_and_adjoint(torch_cuda, orc, n, steps, K, kappa):
     """Fused OU forward and the checkpointed reverse-time adjoint against the
     FP64 oracle: positions, checkpoints, loss, dmu, dsigma, dkappa and dx0.
