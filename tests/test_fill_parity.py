@@ -168,6 +168,7 @@ def test_fill_over_2p30_rows_splits_launches(torch_cuda, orc):
     sampled streams."""
     torch = torch_cuda
     n_streams, dps, seed = (1 << 31) + 9, 16, 0x5EED
+    torch.cuda.empty_cache()                   # return blocks cached by earlier tests
     free, _ = torch.cuda.mem_get_info()
     need = n_streams * dps * 4
     if free < need + (8 << 30):
