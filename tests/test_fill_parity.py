@@ -188,3 +188,20 @@ def test_fill_over_2p30_rows_splits_launches(torch_cuda, orc):
         assert np.array_equal(got[i], ref), int(s)
     del out, idx
     torch.cuda.empty_cache()
+
+
+def test_fills_on_concurrent_streams(torch_cuda, orc):
+    """Fills of every generator enqueued on four streams at once (each call
+    builds its own tensor map): every output equals the oracle."""
+    torch = torch_cuda
+    shape = (1000, 8)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    outs = []
+    for rep in range(3):
+        for gen, s in zip(GENS, streams):
+            out = torch.empty(shape[0] * shape[1], dtype=torch.int32, device="cuda")
+            orand.fill(gen, W.U32, 77 + rep, rep, *shape, out=out, stream=s)
+            outs.append((gen, rep, out))
+    torch.cuda.synchronize()
+    for gen, rep, out in outs:
+        assert np.array_equal(to_numpy(out), orc.fill(gen, W.U32, 77 + rep, rep, *shape)), (gen, rep)
