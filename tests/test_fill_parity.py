@@ -205,3 +205,24 @@ def test_fills_on_concurrent_streams(torch_cuda, orc):
     torch.cuda.synchronize()
     for gen, rep, out in outs:
         assert np.array_equal(to_numpy(out), orc.fill(gen, W.U32, 77 + rep, rep, *shape)), (gen, rep)
+
+
+def test_fill_captured_in_a_cuda_graph(torch_cuda, orc):
+    """A tiled fill captured in a CUDA graph (its tensor map is a kernel
+    parameter, copied at capture) replays to the same bits."""
+    torch = torch_cuda
+    shape = (300, 16)
+    out = torch.zeros(shape[0] * shape[1], dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        orand.fill(W.PHILOX, W.U32, 5, 9, *shape, out=out, stream=s)   # configure outside the capture
+    torch.cuda.synchronize()
+    out.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        orand.fill(W.PHILOX, W.U32, 5, 9, *shape, out=out, stream=s)
+    out.zero_()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_numpy(out), orc.fill(W.PHILOX, W.U32, 5, 9, *shape))
