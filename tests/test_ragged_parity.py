@@ -141,6 +141,27 @@ def test_ragged_overlap_check(torch_cuda, monkeypatch):
         orand.fill_ragged(recs, out_bytes=nbytes)
 
 
+def test_ragged_extreme_keys_and_counters(torch_cuda, orc):
+    """Every generator and dtype with seeds 0 and 2^64 - 1, counters 0 and
+    2^32 - 1, and lengths around the group and chunk sizes."""
+    recs = []
+    for gen in (W.PHILOX, W.THREEFRY, W.SQUARES, W.TYCHE):
+        for dt in (W.U32, W.F32_UNIFORM, W.F64_UNIFORM, W.F32_NORMAL):
+            for seed, counter in [(0, 0), (2**64 - 1, 0xFFFFFFFF), (12345, 0xFFFFFFFF)]:
+                for length in (1, 3, 17, 4096 + 5):
+                    recs.append((gen, dt, seed, counter, 0, length, 0))
+    recs = np.array(recs, dtype=W.REQUEST_DTYPE)
+    off = 0
+    for r in recs:
+        off = (off + 15) // 16 * 16
+        r["out_offset_bytes"] = off
+        off += int(r["length"]) * W.ELEM_BYTES[int(r["dtype"])]
+    out = orand.fill_ragged(recs, out_bytes=off + 16)
+    host = out.cpu().numpy()
+    for r in recs:
+        check_request(orc, host, r)
+
+
 def test_ragged_empty_and_zero_length(torch_cuda, orc):
     recs, nbytes = mixed_requests(20, 5, seed=5)
     recs["length"][::3] = 0
