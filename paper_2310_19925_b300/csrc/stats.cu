@@ -9,10 +9,13 @@
 //   tuple_kernel         grid-stride over tuples; per-CTA shared-memory
 //                        histogram (a column per lane for up to 256 cells),
 //                        flushed once per CTA.
-//   gap_span_kernel      one warp per span of 8192 words, read 32 words at a
-//                        time (coalesced); a ballot of the hits gives each
-//                        hit's distance to the previous one by bit scans.
-//                        The span's first and last hit go to scratch.
+//   gap_span_vec_kernel  one warp per span of 8192 words, read 128 words at a
+//                        time (a 16-byte load per lane); a ballot of the
+//                        lanes with hits and one shuffle give each hit's
+//                        distance to the previous one.  gap_span_kernel
+//                        reads 32 words at a time, for words that are not
+//                        16-byte aligned.  The span's first and last hit go
+//                        to scratch.
 //   gap_stitch_kernel    the gap before each span's first hit, from the
 //                        previous non-empty span or the carried run.
 //   gap_carry_kernel     the run of non-hits after the piece's last hit.
@@ -125,6 +128,79 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 __device__ __forceinline__ bool gap_hit(uint32_t x, uint64_t lo, uint64_t hi)
 {
     return (uint64_t)x >= lo && (uint64_t)x < hi;
+}
+
+// The same per span with each lane reading four consecutive words as one
+// 16-byte load (the words must be 16-byte aligned): a step covers 128 words;
+// a hit's previous hit is in its own lane (a lower word), else in the
+// nearest lower lane with a hit (its last hit, by a shuffle), else the
+// span's running last hit.
+__global__ void __launch_bounds__(256) gap_span_vec_kernel(const uint32_t *__restrict__ w, uint64_t n, uint64_t lo,
+                                                           uint64_t hi, uint32_t t_max,
+                                                           unsigned long long *__restrict__ counts,
+                                                           uint32_t *__restrict__ span_first,
+                                                           uint32_t *__restrict__ span_last, uint64_t n_spans)
+{
+    extern __shared__ uint32_t hist[];
+    for (uint32_t i = threadIdx.x; i <= t_max; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    constexpr uint32_t kSteps = kGapSpan / 128;
+    for (uint64_t sp = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); sp < n_spans; sp += warps) {
+        const uint64_t start = sp * kGapSpan;
+        uint32_t first = kNone, last = kNone;  // span-local offsets, warp-uniform
+        for (uint32_t it0 = 0; it0 < kSteps; it0 += 2) {
+            if (start + (uint64_t)it0 * 128 >= n) break;
+            uint32_t hm[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {  // both steps' loads first
+                const uint64_t idx = start + (uint64_t)(it0 + u) * 128 + lane * 4u;
+                uint32_t v[4];
+                if (idx + 3 < n) {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(w + idx));
+                    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v[j] = idx + j < n ? __ldg(w + idx + j) : 0u;
+                }
+                uint32_t h = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) h |= (idx + j < n && gap_hit(v[j], lo, hi)) ? 1u << j : 0u;
+                hm[u] = h;
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const uint32_t it = it0 + u;
+                const uint32_t h = hm[u];
+                const uint32_t mask = __ballot_sync(0xFFFFFFFFu, h != 0u);
+                if (mask == 0u) continue;
+                // the last hit of the nearest lower lane that has one
+                const uint32_t below = mask & ((1u << lane) - 1u);
+                const uint32_t src = below ? 31u - __clz(below) : lane;
+                const uint32_t hs = __shfl_sync(0xFFFFFFFFu, h, src);
+                if (h) {
+                    uint32_t prev = below ? it * 128 + src * 4 + (31u - __clz(hs)) : last;
+                    for (uint32_t b = h; b; b &= b - 1) {
+                        const uint32_t pos = it * 128 + lane * 4 + (__ffs(b) - 1);
+                        if (prev != kNone) atomicAdd(&hist[min(pos - prev - 1u, t_max)], 1u);
+                        prev = pos;
+                    }
+                }
+                const uint32_t fl = __ffs(mask) - 1, ll = 31u - __clz(mask);
+                const uint32_t hf = __shfl_sync(0xFFFFFFFFu, h, fl), hl = __shfl_sync(0xFFFFFFFFu, h, ll);
+                if (first == kNone) first = it * 128 + fl * 4 + (__ffs(hf) - 1);
+                last = it * 128 + ll * 4 + (31u - __clz(hl));
+            }
+        }
+        if (lane == 0) {
+            span_first[sp] = first;
+            span_last[sp] = last;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i <= t_max; i += blockDim.x)
+        if (hist[i]) atomicAdd(&counts[i], (unsigned long long)hist[i]);
 }
 
 // Per span: gaps between hits inside the span into the histogram, and the
@@ -501,8 +577,12 @@ orand_status_t orand_stat_gaps(orand_ctx_t ctx, const uint32_t *words, uint64_t 
     if ((st = current_device(&info)) != ORAND_OK) return st;
     const size_t smem = (size_t)(t_max + 1) * sizeof(uint32_t);
     const unsigned grid = grid_for(n_spans * 32, 256, info.sm_count, 8);
-    gap_span_kernel<<<grid, 256, smem, stream>>>(words, n_words, lo, hi, t_max, (unsigned long long *)counts,
-                                                 span_first, span_last, n_spans);
+    if ((uintptr_t)words % 16 == 0)
+        gap_span_vec_kernel<<<grid, 256, smem, stream>>>(words, n_words, lo, hi, t_max,
+                                                         (unsigned long long *)counts, span_first, span_last, n_spans);
+    else
+        gap_span_kernel<<<grid, 256, smem, stream>>>(words, n_words, lo, hi, t_max, (unsigned long long *)counts,
+                                                     span_first, span_last, n_spans);
     if ((st = launch_status()) != ORAND_OK) return st;
     gap_stitch_kernel<<<(unsigned)ceil_div(n_spans, 256), 256, 0, stream>>>(
         span_first, span_last, n_spans, (const unsigned long long *)carry, t_max, (unsigned long long *)counts);

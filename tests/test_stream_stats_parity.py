@@ -68,10 +68,14 @@ def test_tuples_exact(torch_cuda, n, t, bits, shift, stride):
                                            (8192, 0, 1 << 32, 16)])
 def test_gaps_exact(torch_cuda, n, lo, hi, t_max):
     w = pcg(n, 3)
-    c, carry = orand.stat_gaps(dev_words(torch_cuda, w), lo, hi, t_max)
     want, wcarry = S.gap_counts(w, lo, hi, t_max)
-    assert np.array_equal(c.cpu().numpy().astype(np.uint64), want)
-    assert int(carry.item()) & (2**64 - 1) == (orand.GAP_NO_HIT if wcarry is None else wcarry)
+    # 16-byte-aligned words (four-word loads) and words one element past
+    # that (one-word loads)
+    padded = dev_words(torch_cuda, np.concatenate([np.zeros(1, np.uint32), w]))
+    for words in (dev_words(torch_cuda, w), padded[1:]):
+        c, carry = orand.stat_gaps(words, lo, hi, t_max)
+        assert np.array_equal(c.cpu().numpy().astype(np.uint64), want)
+        assert int(carry.item()) & (2**64 - 1) == (orand.GAP_NO_HIT if wcarry is None else wcarry)
 
 
 def test_gaps_in_pieces_with_device_carry(torch_cuda):
