@@ -6,7 +6,10 @@
 //
 //   micro_stream_kernel  one thread per (iteration, particle) micro-stream;
 //                        a warp writes 32 * draws consecutive words.
-//   tuple_kernel         grid-stride over tuples; per-CTA shared-memory
+//   tuple_vec_kernel     non-overlapping tuples of 16-byte-aligned words,
+//                        four tuples per thread as t 16-byte loads;
+//                        tuple_kernel grid-strides over single tuples
+//                        otherwise.  Both keep a per-CTA shared-memory
 //                        histogram (a column per lane for up to 256 cells),
 //                        flushed once per CTA.
 //   gap_span_vec_kernel  one warp per span of 8192 words, read 128 words at a
@@ -76,9 +79,6 @@ __global__ void __launch_bounds__(256) micro_stream_kernel(MicroArgs a)
 
 // --------------------------------------------------------------- tuples
 
-// LANES = 32: cells of at most 256, each lane counting in its own column
-// (hist[cell * 32 + lane]), so a warp's atomics never share a bank or an
-// address.  LANES = 1: one column, for up to 2^14 cells.
 constexpr int kTupleUnroll = 8;  // tuples per thread per pass, all loads issued before the atomics
 
 // LANES = 32: cells of at most 256, each lane counting in its own column
@@ -117,6 +117,88 @@ __global__ void __launch_bounds__(256) tuple_kernel(const uint32_t *__restrict__
         for (uint32_t l = 0; l < (uint32_t)LANES; ++l) v += hist[c * LANES + l];
         if (v) atomicAdd(&counts[c], v);
     }
+}
+
+// Non-overlapping tuples (stride = t) of 16-byte-aligned words: four tuples
+// (4t words) per thread per pass as t 16-byte loads, two passes' loads in
+// flight; the tuples after the last whole group of four go to the first
+// threads of block 0.
+template <int LANES, int T>
+__global__ void __launch_bounds__(256) tuple_vec_kernel(const uint32_t *__restrict__ w, uint64_t n_tuples,
+                                                        uint32_t bits, uint32_t shift, uint32_t cells,
+                                                        unsigned long long *__restrict__ counts)
+{
+    extern __shared__ uint32_t hist[];
+    for (uint32_t i = threadIdx.x; i < cells * LANES; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const uint32_t mask = (1u << bits) - 1u;
+    const uint32_t col = LANES == 1 ? 0u : (threadIdx.x & 31u);
+    const uint64_t n4 = n_tuples / 4;  // groups of four tuples = T quads of words
+    const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+    const uint4 *w4 = reinterpret_cast<const uint4 *>(w);
+    auto field = [&](uint32_t x) { return (x >> shift) & mask; };
+    auto count_group = [&](const uint4 (&v)[T]) {
+        const uint32_t *x = reinterpret_cast<const uint32_t *>(v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t cell = 0;
+#pragma unroll
+            for (int i = 0; i < T; ++i) cell = (cell << bits) | field(x[k * T + i]);
+            atomicAdd(&hist[cell * LANES + col], 1u);
+        }
+    };
+    for (uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g0 < n4; g0 += 2 * gstride) {
+        uint4 v0[T], v1[T];
+        const bool ok1 = g0 + gstride < n4;
+#pragma unroll
+        for (int i = 0; i < T; ++i) v0[i] = __ldg(w4 + g0 * T + i);
+        if (ok1) {
+#pragma unroll
+            for (int i = 0; i < T; ++i) v1[i] = __ldg(w4 + (g0 + gstride) * T + i);
+        }
+        count_group(v0);
+        if (ok1) count_group(v1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n_tuples - n4 * 4) {
+        const uint64_t m = n4 * 4 + threadIdx.x;
+        uint32_t cell = 0;
+#pragma unroll
+        for (int i = 0; i < T; ++i) cell = (cell << bits) | field(__ldg(w + m * T + i));
+        atomicAdd(&hist[cell * LANES + col], 1u);
+    }
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) {
+        unsigned long long v = 0;
+        for (uint32_t l = 0; l < (uint32_t)LANES; ++l) v += hist[c * LANES + l];
+        if (v) atomicAdd(&counts[c], v);
+    }
+}
+
+template <int LANES>
+static void launch_tuple_vec(uint32_t t, unsigned grid, size_t smem, cudaStream_t stream, const uint32_t *wp,
+                             uint64_t nt, uint32_t bits, uint32_t shift, uint32_t cells, unsigned long long *counts)
+{
+    switch (t) {
+    case 1: tuple_vec_kernel<LANES, 1><<<grid, 256, smem, stream>>>(wp, nt, bits, shift, cells, counts); break;
+    case 2: tuple_vec_kernel<LANES, 2><<<grid, 256, smem, stream>>>(wp, nt, bits, shift, cells, counts); break;
+    case 3: tuple_vec_kernel<LANES, 3><<<grid, 256, smem, stream>>>(wp, nt, bits, shift, cells, counts); break;
+    default: tuple_vec_kernel<LANES, 4><<<grid, 256, smem, stream>>>(wp, nt, bits, shift, cells, counts); break;
+    }
+}
+
+template <int LANES>
+static orand_status_t tuple_smem_opt_in(size_t smem)
+{
+    ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel<LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_vec_kernel<LANES, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_vec_kernel<LANES, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_vec_kernel<LANES, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_vec_kernel<LANES, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    return ORAND_OK;
 }
 
 // ----------------------------------------------------------------- gaps
@@ -541,15 +623,18 @@ orand_status_t orand_stat_tuples(const uint32_t *words, uint64_t n_words, uint32
     const bool lanes = cells <= 256;
     const size_t smem = (size_t)cells * (lanes ? 32 : 1) * sizeof(uint32_t);
     if (smem > 48 * 1024) {
-        if (lanes) ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        else ORAND_CUDA_TRY(cudaFuncSetAttribute(tuple_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if ((st = lanes ? tuple_smem_opt_in<32>(smem) : tuple_smem_opt_in<1>(smem)) != ORAND_OK) return st;
     }
     // Per-CTA u32 counters: launch pieces small enough that no CTA passes 2^31.
     const uint64_t piece = 1ull << 36;
     for (uint64_t m0 = 0; m0 < n_tuples; m0 += piece) {
         const uint64_t nt = n_tuples - m0 < piece ? n_tuples - m0 : piece;
         const unsigned grid = grid_for(nt, 256, info.sm_count, 4);
-        if (lanes)
+        const uint32_t *wp = words + m0 * stride;
+        if (stride == t && (uintptr_t)wp % 16 == 0) {
+            if (lanes) launch_tuple_vec<32>(t, grid, smem, stream, wp, nt, bits, shift, cells, (unsigned long long *)counts);
+            else launch_tuple_vec<1>(t, grid, smem, stream, wp, nt, bits, shift, cells, (unsigned long long *)counts);
+        } else if (lanes)
             tuple_kernel<32><<<grid, 256, smem, stream>>>(words + m0 * stride, nt, t, bits, shift, stride, cells,
                                                          (unsigned long long *)counts);
         else

@@ -54,13 +54,18 @@ def test_micro_streams_bit_exact(torch_cuda, orc, gen, draws):
 @pytest.mark.parametrize("n,t,bits,shift,stride", [(100003, 1, 8, 24, 1), (100003, 1, 8, 0, 1),
                                                    (99999, 2, 6, 26, 2), (99999, 3, 4, 28, 3),
                                                    (77777, 4, 3, 1, 4), (5000, 1, 14, 18, 1),
-                                                   (4099, 2, 7, 3, 1), (2, 3, 4, 28, 3), (3, 3, 4, 28, 3)])
+                                                   (4099, 2, 7, 3, 1), (2, 3, 4, 28, 3), (3, 3, 4, 28, 3),
+                                                   (3, 1, 8, 24, 1), (6, 1, 4, 0, 1)])
 def test_tuples_exact(torch_cuda, n, t, bits, shift, stride):
     w = pcg(n)
-    c = orand.stat_tuples(dev_words(torch_cuda, w), t, bits, shift, stride)
-    c = orand.stat_tuples(dev_words(torch_cuda, w[: n // 2]), t, bits, shift, stride, counts=c)  # accumulates
     want = S.tuple_counts(w, t, bits, shift, stride) + S.tuple_counts(w[: n // 2], t, bits, shift, stride)
-    assert np.array_equal(c.cpu().numpy().astype(np.uint64), want)
+    # 16-byte-aligned words (the four-word loads of single-word tuples) and
+    # words one element past that (one-word loads)
+    padded = dev_words(torch_cuda, np.concatenate([np.zeros(1, np.uint32), w]))
+    for words in (dev_words(torch_cuda, w), padded[1:]):
+        c = orand.stat_tuples(words, t, bits, shift, stride)
+        c = orand.stat_tuples(words[: n // 2], t, bits, shift, stride, counts=c)  # accumulates
+        assert np.array_equal(c.cpu().numpy().astype(np.uint64), want)
 
 
 @pytest.mark.parametrize("n,lo,hi,t_max", [(8192 * 3 + 77, 0, 1 << 28, 64), (100000, 3 << 30, 1 << 32, 8),
