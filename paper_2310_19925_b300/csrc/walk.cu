@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 
 // ------------------------------------------------------------------ 2D walk
 
-// The 2D kernel is bound by instruction issue (74 operations per
+// The 2D kernel is bound by instruction issue (67 operations per
 // particle-step, nearly all of them the Philox rounds and Box-Muller).  One
 // particle per thread; the position sum is compensated per block of
 // kSumBlock steps (plain FMA sums inside a block, a Kahan add of each block
@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 // bound of one block per SM, ptxas keeps the round keys in registers.
 // Measured on B300 (full walk, 2^24 x 10^4): 433.9 ms, against 437.9 with
 // two particles per thread (unroll 2, 90 registers); three or four per
-// thread measured slower still.
+// thread measured slower still, and so did launch bounds that fit 32 or 40
+// warps per SM (436.6-446.1 ms).
 constexpr int kWalk2dBlock = 256;
 constexpr uint32_t kSumBlock = 16;
 
@@ -193,10 +194,10 @@ __global__ void __launch_bounds__(kWalkBlock) walk3d_init_kernel(Walk3dArgs a, f
 // is Kahan-added to the position, as in the 2D kernel.  OU: the drift
 // mu - kappa x is evaluated at the current position x + s (s the block's
 // partial sum); without it the constant drift mu dt is added once per block.
-// Launch bounds (measured on B300, forward + adjoint of 2^22 x 4096): one
-// block per SM for the constant drift (86 and 83 registers, 142.4 ms; three
-// blocks: 143.7 ms), three for OU (78 and 80 registers, 158.3 ms; one
-// block: 159.9 ms).
+// Launch bounds (measured on B300, forward + adjoint of 2^22 x 4096, with
+// the walks' earlier map): one block per SM for the constant drift (86 and
+// 83 registers, 142.4 ms; three blocks: 143.7 ms), three for OU (78 and 80
+// registers, 158.3 ms; one block: 159.9 ms).
 template <bool OU>
 __global__ void __launch_bounds__(kWalkBlock, OU ? 3 : 1) walk3d_fwd_kernel(Walk3dArgs a, const float *__restrict__ x0_in,
                                                                float *__restrict__ xT, float *__restrict__ ckpt,
