@@ -763,7 +763,7 @@ def main():
     rooflines["fill_tile_kernel<philox,u32>"] = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
         "traffic": traffic, "share_of_step": row_table[head.name]["share_of_step"],
-        "kernel": "fill_tile_kernel<philox4x32_10, u32, R=4> (swizzled tile, TMA tensor store)",
+        "kernel": "fill_tile_kernel<philox4x32_10, u32, R=4, whole rows> (swizzled tile, TMA tensor store)",
         "peak_kind": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"}
     # `roofline`: the dominant kernel of the step, the 2D walk (issue-bound),
     # with the DRAM bytes of one launch from ncu (the 2^24 positions; the

@@ -79,6 +79,11 @@ __global__ void __launch_bounds__(256) fill_random_access_kernel(FillArgs a)
 // partial row (fewer than 8) are stored directly by the threads that make
 // them.
 //
+// Each (generator, dtype, R, shape) has two kernels: the general one, and
+// one for launches where every stream is a single run and the output is
+// whole rows (the usual case, e.g. 16 words per stream), which skips the
+// stream split and the partial-row stores.
+//
 // Launch shape per row (measured on B300): the light, HBM-bound Philox u32 and
 // FP32-uniform fills use T = 128 and TR = 8 / R, which halves the per-tile
 // barrier and bookkeeping cost per group.  Every other fill is bound by the
@@ -146,11 +151,34 @@ struct StreamGen<ORAND_SQUARES32> {
 
 // Run lr of this launch (global run r = r_first + lr): groups [q*R, q*R + R)
 // of stream s.  Chunk i goes to the shared address a0 ^ (i * 16) and, when
-// the run lies in a final partial row, straight to HBM as well.
-template <int GEN, int DT, int R>
+// the run lies in a final partial row, straight to HBM as well.  WHOLE: every
+// stream is one run (run r is stream r) and the launch's output is whole
+// rows, so neither the stream split nor the partial-row store is needed
+// (measured on B300, Philox u32 2^24 x 16: 0.172 ms against 0.182).
+template <int GEN, int DT, int R, bool WHOLE>
 __device__ __forceinline__ void fill_run(const TileArgs &a, uint64_t lr, uint32_t a0)
 {
     const uint64_t r = a.r_first + lr;
+    if constexpr (WHOLE) {
+        auto put = [&](int i, uint4 bits) { st_shared_v4(a0 ^ ((uint32_t)i << 4), bits); };
+        if constexpr (GEN == ORAND_TYCHE) {
+            orand::TycheState st = orand::tyche_init(a.seed ^ r, a.counter);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                uint4 w;
+                w.x = orand::tyche_next(st);
+                w.y = orand::tyche_next(st);
+                w.z = orand::tyche_next(st);
+                w.w = orand::tyche_next(st);
+                put(i, group_bits<DT>(w));
+            }
+        } else {
+            const StreamGen<GEN> sg(a.seed ^ r, a.counter);
+#pragma unroll
+            for (int i = 0; i < R; ++i) put(i, group_bits<DT>(sg.group((uint32_t)i)));
+        }
+        return;
+    }
     uint64_t s, q;
     if (a.rps_shift >= 0) {
         s = r >> a.rps_shift;
@@ -192,7 +220,7 @@ __device__ __forceinline__ void fill_run(const TileArgs &a, uint64_t lr, uint32_
     }
 }
 
-template <int GEN, int DT, int R, int T, int TR>
+template <int GEN, int DT, int R, int T, int TR, bool WHOLE>
 __global__ void __launch_bounds__(T) fill_tile_kernel(const __grid_constant__ CUtensorMap map, TileArgs a)
 {
     constexpr uint32_t kRunsPerTile = (uint32_t)T * TR;
@@ -216,7 +244,7 @@ __global__ void __launch_bounds__(T) fill_tile_kernel(const __grid_constant__ CU
             const uint32_t row = (slot * R) >> 3;
             const uint32_t a0 = sb + row * 128u + ((((slot * R) & 7u) ^ (row & 7u)) << 4);
             const uint64_t lr = t * kRunsPerTile + slot;
-            if (lr < a.n_runs) fill_run<GEN, DT, R>(a, lr, a0);
+            if (lr < a.n_runs) fill_run<GEN, DT, R, WHOLE>(a, lr, a0);
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -274,21 +302,22 @@ static orand_status_t launch_tile_shape(TileArgs a, const DeviceInfo &info, cuda
     // The shared-memory opt-in is per device: one bit per ordinal (the call is
     // idempotent, so a race only repeats it).  Ordinals past 63 set it on
     // every launch.
+    // Kernel 1 serves launches where every stream is one run and the output
+    // is whole rows (see fill_run); kernel 0 serves the rest.
+    void (*const kernel[2])(const CUtensorMap, TileArgs) = {fill_tile_kernel<GEN, DT, R, T, TR, false>,
+                                                            fill_tile_kernel<GEN, DT, R, T, TR, true>};
     static std::atomic<uint64_t> configured{0};
     const uint64_t bit = info.device < 64 ? 1ull << info.device : 0;
     if (bit == 0 || !(configured.load(std::memory_order_relaxed) & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(fill_tile_kernel<GEN, DT, R, T, TR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_status(e);
+        for (int k = 0; k < 2; ++k) {
+            cudaError_t e = cudaFuncSetAttribute(kernel[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
         configured.fetch_or(bit, std::memory_order_relaxed);
     }
     const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (encode == nullptr) return ORAND_ERR_CUDA;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_tile_kernel<GEN, DT, R, T, TR>, T,
-                                                                  smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (per_sm < 1) per_sm = 1;
+    int per_sm[2] = {0, 0};  // resident CTAs per SM, looked up when a kernel is first used
     const uint64_t total_runs = a.n_runs;
     const uint64_t runs_per_launch = kMaxRowsPerLaunch * 8 / R;
     uint4 *const out0 = a.out;
@@ -313,9 +342,15 @@ static orand_status_t launch_tile_shape(TileArgs a, const DeviceInfo &info, cuda
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return ORAND_ERR_CUDA;
-        uint64_t grid = (uint64_t)per_sm * info.sm_count;
+        const int k = (a.rps == 1 && p.n_runs * R % 8 == 0) ? 1 : 0;
+        if (per_sm[k] == 0) {
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[k], kernel[k], T, smem);
+            if (e != cudaSuccess) return cuda_status(e);
+            if (per_sm[k] < 1) per_sm[k] = 1;
+        }
+        uint64_t grid = (uint64_t)per_sm[k] * info.sm_count;
         if (grid > p.n_tiles) grid = p.n_tiles;
-        fill_tile_kernel<GEN, DT, R, T, TR><<<(unsigned)grid, T, smem, stream>>>(map, p);
+        kernel[k]<<<(unsigned)grid, T, smem, stream>>>(map, p);
         const orand_status_t st = launch_status();
         if (st != ORAND_OK) return st;
     }

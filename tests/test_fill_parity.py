@@ -55,8 +55,10 @@ def gpu_fill(torch, gen, dtype, seed, counter, n_streams, dps, offset_elems=0):
 
 # (7, 4): under one 128-byte row (untiled); (9, 4), (65, 8), (3, 40): full rows
 # plus a partial row; (2, 16): exactly one row; (3, 40): 5 runs per stream.
+# One run per stream over whole rows (the tiled kernel's specialised form):
+# (64, 4), (1000, 8), (100, 16), (513, 32) with runs of 1, 2, 4 and 8 groups.
 SHAPES = [(1, 1), (3, 5), (257, 4), (100, 16), (33, 67), (1000, 8), (5, 130), (77, 96), (300, 48), (513, 32),
-          (7, 4), (9, 4), (2, 16), (65, 8), (3, 40)]
+          (7, 4), (9, 4), (2, 16), (65, 8), (3, 40), (64, 4)]
 
 
 @pytest.mark.parametrize("gen", GENS)
@@ -160,14 +162,16 @@ def test_fill_large_workload_sampled(torch_cuda, orc, gen, dtype):
     torch.cuda.empty_cache()
 
 
-def test_fill_over_2p30_rows_splits_launches(torch_cuda, orc):
-    """A u32 fill of 2^31 + 9 streams x 16 words (128 GiB + 576 B): more than
-    the 2^30 128-byte rows one tensor-store launch addresses, so the tiled
-    path runs a second launch of 9 streams, whose last 4 chunks form a
-    partial row.  Exact on the streams around the split and the end, and on
-    sampled streams."""
+@pytest.mark.parametrize("extra", [9, 16])
+def test_fill_over_2p30_rows_splits_launches(torch_cuda, orc, extra):
+    """A u32 fill of 2^31 + extra streams x 16 words (128 GiB + 64 B per extra
+    stream): more than the 2^30 128-byte rows one tensor-store launch
+    addresses, so the tiled path runs a second launch of the extra streams,
+    starting at stream 2^31.  With 9 its last 4 chunks form a partial row;
+    with 16 it is whole rows, which the specialised kernel serves.  Exact on
+    the streams around the split and the end, and on sampled streams."""
     torch = torch_cuda
-    n_streams, dps, seed = (1 << 31) + 9, 16, 0x5EED
+    n_streams, dps, seed = (1 << 31) + extra, 16, 0x5EED
     torch.cuda.empty_cache()                   # return blocks cached by earlier tests
     free, _ = torch.cuda.mem_get_info()
     need = n_streams * dps * 4
