@@ -345,12 +345,14 @@ __device__ __forceinline__ float bm_radius(uint32_t w0)
 {
     const uint32_t k = (w0 >> 8) + 1u;                         /* 1 .. 2^24 */
     const uint32_t bits = __float_as_uint(__uint2float_rn(k)); /* exact */
-    int e = (int)(bits >> 23) - 127;
-    uint32_t mb = (bits & 0x007FFFFFu) | 0x3F800000u;          /* f in [1, 2) */
-    const uint32_t halve = mb >= 0x3FB504F3u ? 1u : 0u;       /* f >= sqrt(2): halve f */
-    mb -= halve << 23;
-    e += (int)halve;
-    const float g = __uint_as_float(mb) - 1.0f;                /* exact */
+    /* k = 2^e f with f in [sqrt(2)/2, sqrt(2)): subtracting the bit pattern of
+     * sqrt(2)/2 (0x3F3504F3) carries into the exponent field exactly when the
+     * significand is >= sqrt(2), so the exponent field is e and the low 23
+     * bits, added back to the pattern, are f's.  The extra 24 << 23 gives
+     * e - 24 directly (u1 = k 2^-24); the shift is arithmetic. */
+    const uint32_t t = bits - 0x4B3504F3u;
+    const float E = (float)((int)t >> 23);                     /* ln u1 = E ln 2 + ln f */
+    const float g = __uint_as_float((t & 0x007FFFFFu) + 0x3F3504F3u) - 1.0f; /* f - 1, exact */
     float p = fmaf(bm::PL8, g, bm::PL7);
     p = fmaf(p, g, bm::PL6);
     p = fmaf(p, g, bm::PL5);
@@ -360,7 +362,6 @@ __device__ __forceinline__ float bm_radius(uint32_t w0)
     p = fmaf(p, g, bm::PL1);
     p = fmaf(p, g, bm::PL0);
     const float lnf = fmaf(g * g, p, g);
-    const float E = (float)(e - 24);                           /* ln u1 = E ln 2 + ln f */
     const float lnu = fmaf(E, bm::LN2_HI, fmaf(E, bm::LN2_LO, lnf));
     const float x = fmaf(-2.0f, lnu, 0.0f);                    /* -2 ln u1 >= +0 */
     /* sqrt(x) without the special-case branch of the IEEE square root:
@@ -375,12 +376,14 @@ __device__ __forceinline__ float bm_radius(uint32_t w0)
 }
 
 /* (cos, sin)(2 pi u2), u2 = (w1 >> 8) * 2^-24: quadrant q = round(4 u2),
- * r = 2 u2 - q/2 in [-1/4, 1/4] exactly, then a signed swap by q mod 4. */
+ * r = 2 u2 - q/2 in [-1/4, 1/4] exactly, then a signed swap by q mod 4.
+ * With a = w1 + 2^29 (mod 2^32; adding half a quadrant at bit 29 leaves the
+ * low 8 bits alone), q mod 4 is a's top two bits and (4 u2 - q) 2^22 is its
+ * bits 8..29 minus 2^21. */
 __device__ __forceinline__ void bm_cos_sin(uint32_t w1, float *c, float *s)
 {
-    const uint32_t m = w1 >> 8;                                /* 4 u2 = m 2^-22 */
-    const uint32_t q = (m + (1u << 21)) >> 22;
-    const float r = (float)(int)(m - (q << 22)) * 0x1p-23f;    /* exact */
+    const uint32_t a = w1 + (1u << 29);
+    const float r = (float)((int)((a >> 8) & 0x3FFFFFu) - (1 << 21)) * 0x1p-23f; /* exact */
     const float t = r * r;
     float qs = fmaf(bm::QS3, t, bm::QS2);
     qs = fmaf(qs, t, bm::QS1);
@@ -391,10 +394,10 @@ __device__ __forceinline__ void bm_cos_sin(uint32_t w1, float *c, float *s)
     qc = fmaf(qc, t, bm::QC1);
     qc = fmaf(qc, t, bm::QC0);
     const float cs = fmaf(t, qc, 1.0f);
-    const bool swap = q & 1u;
-    const uint32_t a = __float_as_uint(swap ? cs : sn), b = __float_as_uint(swap ? sn : cs);
-    *s = __uint_as_float(a ^ ((q & 2u) << 30));                /* negate sin for q = 2, 3 */
-    *c = __uint_as_float(b ^ (((q + 1u) & 2u) << 30));         /* negate cos for q = 1, 2 */
+    const bool swap = (a >> 30) & 1u;
+    const uint32_t vs = __float_as_uint(swap ? cs : sn), vc = __float_as_uint(swap ? sn : cs);
+    *s = __uint_as_float(vs ^ (a & 0x80000000u));              /* negate sin for q = 2, 3 */
+    *c = __uint_as_float(vc ^ ((a ^ (a << 1)) & 0x80000000u)); /* negate cos for q = 1, 2 */
 }
 
 /* Box-Muller pair (r cos 2 pi u2, r sin 2 pi u2) from two words. */
