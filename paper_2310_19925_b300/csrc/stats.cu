@@ -392,9 +392,10 @@ __global__ void gap_carry_kernel(const uint32_t *__restrict__ span_last, uint64_
 // finds a representative of its own value is a repeat; one that finds
 // another value tries again in the next round.  Each round resolves at
 // least the last writer of every slot, so the rounds end (about three for
-// random spacings).  Measured on B300 (11,994 samples of 4096 keys): 0.49 ms
+// random spacings).  Measured on B300 (11,994 samples of 4096 keys): 0.45 ms
 // per launch, against 0.60 with a linear-probing hash set built by
-// compare-and-swap and 0.53 with 2n slots.
+// compare-and-swap, 0.53 with 2n slots and 0.49 with every round visiting
+// all of a thread's spacings.
 
 constexpr int kBirthdayBlock = 512;
 constexpr uint32_t kMaxBucket = 64;
@@ -552,30 +553,39 @@ __global__ void __launch_bounds__(kBirthdayBlock, 3) birthday_kernel(const uint3
                 }
             }
         }
-        for (;;) {
+        // Round 1 reads back every spacing (unrolled); later rounds visit
+        // only a thread's unresolved spacings, usually none or one.
+        __syncthreads();
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxPer; ++k) {
+            if ((pending >> k) & 1u) {
+                const uint32_t i = threadIdx.x + k * blockDim.x;
+                const uint32_t v = sp[i];
+                const uint32_t j = slot[(v * 0x9E3779B1u) >> (32 - tbits)];
+                if (j == i) {
+                    ++distinct;                  // the representative of its value
+                    pending &= ~(1u << k);
+                } else if (sp[j] == v) {
+                    pending &= ~(1u << k);       // a repeat of a represented value
+                }
+            }
+        }
+        while (__syncthreads_or(pending != 0u)) {
+            for (uint32_t q = pending; q != 0u; q &= q - 1u) {
+                const uint32_t i = threadIdx.x + (uint32_t)(__ffs(q) - 1) * blockDim.x;
+                slot[(sp[i] * 0x9E3779B1u) >> (32 - tbits)] = (uint16_t)i;
+            }
             __syncthreads();
-#pragma unroll
-            for (uint32_t k = 0; k < kMaxPer; ++k) {
-                if ((pending >> k) & 1u) {
-                    const uint32_t i = threadIdx.x + k * blockDim.x;
-                    const uint32_t v = sp[i];
-                    const uint32_t j = slot[(v * 0x9E3779B1u) >> (32 - tbits)];
-                    if (j == i) {
-                        ++distinct;                  // the representative of its value
-                        pending &= ~(1u << k);
-                    } else if (sp[j] == v) {
-                        pending &= ~(1u << k);       // a repeat of a represented value
-                    }
-                }
+            uint32_t left = 0u;
+            for (uint32_t q = pending; q != 0u; q &= q - 1u) {
+                const uint32_t k = (uint32_t)(__ffs(q) - 1);
+                const uint32_t i = threadIdx.x + k * blockDim.x;
+                const uint32_t v = sp[i];
+                const uint32_t j = slot[(v * 0x9E3779B1u) >> (32 - tbits)];
+                if (j == i) ++distinct;
+                else if (sp[j] != v) left |= 1u << k;
             }
-            if (!__syncthreads_or(pending != 0u)) break;
-#pragma unroll
-            for (uint32_t k = 0; k < kMaxPer; ++k) {
-                if ((pending >> k) & 1u) {
-                    const uint32_t i = threadIdx.x + k * blockDim.x;
-                    slot[(sp[i] * 0x9E3779B1u) >> (32 - tbits)] = (uint16_t)i;
-                }
-            }
+            pending = left;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) distinct += __shfl_down_sync(0xFFFFFFFFu, distinct, o);
