@@ -174,8 +174,8 @@ def test_battery_rejects_planted_correlation(torch_cuda):
 
 
 def test_birthday_extreme_spacings(torch_cuda):
-    """Spacings of exactly 2^32 - 1 (the hash set's empty marker) and 2^32
-    (the wrap spacing when all birthdays are equal), in 32-bit years."""
+    """Spacings of exactly 2^32 - 1 (the largest 32-bit value) and 2^32 (the
+    wrap spacing when all birthdays are equal), in 32-bit years."""
     M = 0xFFFFFFFF
     samples = [[0, M, M, M], [0, M, 0, M], [0, M, 5, 7], [M, M, M, M], [0, 1, 2, 3], [M, 0, 1, M - 1]]
     w = np.array([x for s in samples for x in s], np.uint32)
@@ -188,5 +188,27 @@ def test_birthday_bucket_overflow_falls_back(torch_cuda):
     vary) takes the bounded fallback sort; counts still equal the oracle's."""
     rng = np.random.default_rng(8)
     w = (rng.integers(0, 4096, size=4096 * 6, dtype=np.uint64).astype(np.uint32) | np.uint32(0x5A5A0000))
+    c = orand.stat_birthday(dev_words(torch_cuda, w), 12, 32, 0, 4096)
+    assert np.array_equal(c.cpu().numpy().astype(np.uint64), S.birthday_counts(w, 12, 32, 0, 4096))
+
+
+def test_birthday_colliding_and_repeated_spacings(torch_cuda):
+    """Samples whose spacings take few values, all of which share one slot of
+    the kernel's multiplicative hash (the 4n-slot table of n = 4096), so the
+    distinct spacings are resolved one round at a time and most spacings are
+    repeats.  Counts equal the oracle's."""
+    rng = np.random.default_rng(11)
+    v = np.arange(1, 1 << 19, dtype=np.uint64)
+    slot = ((v * np.uint64(0x9E3779B1)) & np.uint64(0xFFFFFFFF)) >> np.uint64(32 - 14)
+    target = np.bincount(slot.astype(np.int64)).argmax()
+    vals = v[slot == target]                                  # distinct values, one slot
+    assert len(vals) >= 24
+    samples = []
+    for kinds in (len(vals), 8, 1):
+        sp = rng.choice(vals[:kinds], size=4095)
+        keys = np.concatenate([[0], np.cumsum(sp)]).astype(np.uint64) + np.uint64(rng.integers(0, 1 << 20))
+        assert keys[-1] < (1 << 32)
+        samples.append(rng.permutation(keys.astype(np.uint32)))
+    w = np.concatenate(samples)
     c = orand.stat_birthday(dev_words(torch_cuda, w), 12, 32, 0, 4096)
     assert np.array_equal(c.cpu().numpy().astype(np.uint64), S.birthday_counts(w, 12, 32, 0, 4096))
