@@ -130,6 +130,25 @@ def test_walk3d_forward_small(torch_cuda, orc, n, steps, K):
     assert loss.item() == pytest.approx(oloss, rel=GRAD_TOL, abs=1e-12)
 
 
+@pytest.mark.parametrize("seed,p_first", [(0x1234, 2**40 + 3), (2**64 - 1, 2**63 - 700)])
+def test_walk3d_far_keys(torch_cuda, orc, seed, p_first):
+    """Forward and adjoint with a nonzero seed and particle ids far from 0
+    (keys seed ^ (p_first + i) use all 64 bits)."""
+    n, steps, K = 513, 80, 16
+    p = _p(n, steps, K, p_first=p_first, p_total=n, seed=seed)
+    xT, ck, _ = orand.walk3d_forward(p)
+    g = torch_cuda.tensor(1.0, dtype=torch_cuda.float64, device="cuda")
+    dmu, dsig, dx0 = orand.walk3d_backward(p, xT, g)
+    torch_cuda.cuda.synchronize()
+    oxT, ock = orc.walk3d_forward(seed, n, steps, K, _f32(1e-3), MU, 0.5, p_first=p_first, want_ckpt=True)
+    pos_close(to_numpy(xT), oxT)
+    pos_close(to_numpy(ck), ock)
+    odmu, odsig, odx0 = orc.walk3d_adjoint(seed, n, steps, _f32(1e-3), oxT, 2.0, n, p_first=p_first)
+    assert np.allclose(to_numpy(dmu), odmu, rtol=GRAD_TOL, atol=0)
+    assert dsig.item() == pytest.approx(odsig, rel=GRAD_TOL)
+    np.testing.assert_allclose(to_numpy(dx0), odx0, rtol=GRAD_TOL, atol=2.0 / n * POS_TOL)
+
+
 @pytest.mark.parametrize("n,steps", [(1, 3), (777, 200), (1024, 64)])
 def test_walk3d_adjoint_small(torch_cuda, orc, n, steps):
     p = _p(n, steps, p_first=11, p_total=5 * n)
