@@ -15,6 +15,7 @@ from the publications the paper cites for them (§3): Philox/Threefry (Salmon
 et al. 2011), Squares (Widynski 2020), Tyche (Neves & Araujo 2011).
 Parity unpinned: the Threefry4x32-20 round function and the Squares round
 order (no outside implementation to compare against in this environment).
+The Squares key derivation (MurmurHash3's 64-bit finaliser) is pinned.
 """
 from __future__ import annotations
 

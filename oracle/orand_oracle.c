@@ -29,8 +29,10 @@
  * Pins (see tests/test_oracle_pins.py): Philox against cuRAND's host Philox
  * generator run as a black box; Tyche's MIX against ChaCha20 from the
  * `cryptography` package; Tyche and Philox constants against their closed
- * forms; maps and Box-Muller against exact edge values and invariants; walks
- * against closed forms and finite differences.  Threefry4x32-20's rotation
+ * forms; the Squares key's MurmurHash3 finaliser against MurmurHash3_x64_128
+ * built from the source scikit-learn ships; maps and Box-Muller against exact
+ * edge values and invariants; walks against closed forms and finite
+ * differences.  Threefry4x32-20's rotation
  * table and injection order and Squares' round order have no outside
  * implementation to compare with here: parity unpinned for those round
  * functions (they are checked by invariants only).

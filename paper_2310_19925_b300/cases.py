@@ -1,6 +1,7 @@
 """Run one hot-path case a few times at a chosen size (profiling and timing).
 
     python -m paper_2310_19925_b300.cases fill --gen 0 --dtype 0 --streams 16777216 --dps 16
+    python -m paper_2310_19925_b300.cases fill --gen -1 --dtype -1     (every generator x dtype)
     python -m paper_2310_19925_b300.cases walk2d --particles 1048576 --steps 1000
     python -m paper_2310_19925_b300.cases walk3d --particles 1048576 --steps 512
     python -m paper_2310_19925_b300.cases ragged --requests 2000 --max-log2 20
@@ -45,8 +46,8 @@ def timed(torch, fn, reps, busy_ms=0.0):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["fill", "walk2d", "walk3d", "ragged", "tyche-chain", "langevin"])
-    ap.add_argument("--gen", type=int, default=0)
-    ap.add_argument("--dtype", type=int, default=0)
+    ap.add_argument("--gen", type=int, default=0, help="fill: generator, -1 for all four in turn")
+    ap.add_argument("--dtype", type=int, default=0, help="fill: dtype, -1 for all four in turn")
     ap.add_argument("--streams", type=int, default=1 << 24)
     ap.add_argument("--dps", type=int, default=16)
     ap.add_argument("--particles", type=int, default=1 << 20)
@@ -67,6 +68,17 @@ def main(argv=None):
 
     sh = torch.cuda.current_stream().cuda_stream
     res = {"case": args.case}
+    if args.case == "fill" and (args.gen < 0 or args.dtype < 0):
+        # Every requested (generator, dtype) in turn, one line each; the
+        # launches run in this order, so an ncu capture of `-c 16` sees one
+        # launch per combination at --reps 1.
+        gens = range(4) if args.gen < 0 else [args.gen]
+        dts = range(4) if args.dtype < 0 else [args.dtype]
+        for g in gens:
+            for d in dts:
+                main(["fill", "--gen", str(g), "--dtype", str(d), "--streams", str(args.streams),
+                      "--dps", str(args.dps), "--reps", str(args.reps)])
+        return
     if args.case == "fill":
         out = torch.empty(args.streams * args.dps, dtype=orand.torch_dtype(args.dtype), device="cuda")
         fn = lambda: orand.orand_fill(args.gen, args.dtype, 0x5EED, 0, args.streams, args.dps, out.data_ptr(), sh)
@@ -74,6 +86,7 @@ def main(argv=None):
         nbytes = out.numel() * out.element_size()
         res.update(gen=args.gen, dtype=args.dtype, streams=args.streams, dps=args.dps,
                    ms=statistics.mean(ts), GBps=nbytes / (statistics.mean(ts) * 1e-3) / 1e9)
+        del out
     elif args.case == "walk2d":
         pos = torch.empty((args.particles, 2), dtype=torch.float32, device="cuda")
         prm = orand.walk2d_params(args.particles, args.steps)

@@ -8,7 +8,10 @@
   floor(2^32/pi).
 * Word->value maps against exact edge values; Box-Muller against the polar
   invariants r^2 = -2 ln u1 and angle = 2 pi u2.
-* Threefry4x32-20 and Squares: no outside implementation exists here
+* The Squares key derivation (MurmurHash3's 64-bit finaliser fmix64)
+  against MurmurHash3_x64_128 from the MurmurHash3 source that scikit-learn
+  ships, compiled here and called as a black box.
+* Threefry4x32-20 and Squares' rounds: no outside implementation exists here
   (parity unpinned for their round functions); they are held to invariants
   (bijectivity through an inverse written here, avalanche, uniformity).
 """
@@ -189,6 +192,10 @@ def _threefry_inverse(out, key):
 
 
 def test_threefry_is_a_bijection_of_the_counter(orc):
+    """The inverse reads the same rotation table and round pairing as the
+    oracle, so this proves only that the oracle's rounds and injections form
+    a bijection that the inverse undoes; it does not pin the table or the
+    injection order against an outside implementation (none exists here)."""
     rng = np.random.default_rng(5)
     for _ in range(50):
         ctr = [int(v) for v in rng.integers(0, 2**32, 4, dtype=np.uint64)]
@@ -238,6 +245,65 @@ def test_avalanche(orc, gen, what):
 def test_squares_key_is_odd(orc):
     for k in [0, 1, 2, 0x5EED, 2**64 - 1, 12345678901234]:
         assert orc.squares_key(k) & 1 == 1
+
+
+def _murmur3_x64_128():
+    """MurmurHash3_x64_128 (Appleby, public domain) from the copy of its
+    source that scikit-learn installs, built into a throw-away library with
+    an extern "C" entry point; None when the source or a C++ compiler is
+    missing."""
+    import shutil
+    import subprocess
+    import tempfile
+
+    try:
+        import sklearn
+    except ImportError:
+        return None
+    src = os.path.join(os.path.dirname(sklearn.__file__), "utils", "src", "MurmurHash3.cpp")
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not os.path.exists(src) or cxx is None:
+        return None
+    d = tempfile.mkdtemp(prefix="murmur3_pin_")
+    shim = os.path.join(d, "shim.cpp")
+    with open(shim, "w") as f:
+        f.write('#include "%s"\n' % src)
+        f.write('extern "C" void murmur3_x64_128(const void *k, int n, uint32_t s, void *o)'
+                ' { MurmurHash3_x64_128(k, n, s, o); }\n')
+    so = os.path.join(d, "libmurmur3_pin.so")
+    r = subprocess.run([cxx, "-O1", "-shared", "-fPIC", "-I", os.path.dirname(src), shim, "-o", so],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        return None
+    lib = ctypes.CDLL(so)
+    lib.murmur3_x64_128.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p]
+    lib.murmur3_x64_128.restype = None
+    return lib
+
+
+def test_squares_key_is_murmur3_fmix64(orc):
+    """The Squares key is fmix64(key64) | 1.  MurmurHash3_x64_128 of an empty
+    input with 32-bit seed s ends by finalising h1 = 2s and h2 = 3s, so its
+    two output words give F(2s) + F(3s) and F(2s) + 2 F(3s), with F the
+    64-bit finaliser: F(3s) = out2 - out1 and F(2s) = 2 out1 - out2.  The
+    inputs reach 3 (2^32 - 1) > 2^33, so the first shift's amount is
+    exercised too (bits 32 and 33 are set), and every later step acts on
+    full 64-bit values."""
+    lib = _murmur3_x64_128()
+    if lib is None:
+        pytest.skip("scikit-learn's MurmurHash3 source or a C++ compiler is missing")
+    M64 = 2**64 - 1
+    rng = np.random.default_rng(2026)
+    seeds = [0, 1, 2, 0x5EED, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFF] + \
+        [int(v) for v in rng.integers(0, 2**32, 200, dtype=np.uint64)]
+    out = (ctypes.c_uint64 * 2)()
+    for s in seeds:
+        lib.murmur3_x64_128(None, 0, s, out)
+        o1, o2 = int(out[0]), int(out[1])
+        f3 = (o2 - o1) & M64
+        f2 = (2 * o1 - o2) & M64
+        assert orc.squares_key(2 * s) == f2 | 1, hex(s)
+        assert orc.squares_key(3 * s) == f3 | 1, hex(s)
 
 
 # ------------------------------------------------------------- stream layout -
