@@ -38,8 +38,14 @@ __device__ __forceinline__ uint4 group_bits(uint4 w)
         return make_uint4(__float_as_uint(orand::u01_f32(w.x)), __float_as_uint(orand::u01_f32(w.y)),
                           __float_as_uint(orand::u01_f32(w.z)), __float_as_uint(orand::u01_f32(w.w)));
     if (DT == ORAND_F64_UNIFORM) {
-        const double da = BRANCH_FREE ? orand::u01_f64_nb(w.x, w.y) : orand::u01_f64(w.x, w.y);
-        const double db = BRANCH_FREE ? orand::u01_f64_nb(w.z, w.w) : orand::u01_f64(w.z, w.w);
+        if (!BRANCH_FREE && __builtin_expect(min(w.x, w.z) >= (1u << 20), 1)) {
+            // Both high words >= 2^20 (all but about 2^-11 of the groups):
+            // the short exact form for both values, one test for the pair.
+            const uint2 a = orand::u01_f64_bits_hi20(w.x, w.y), b = orand::u01_f64_bits_hi20(w.z, w.w);
+            return make_uint4(a.y, a.x, b.y, b.x);
+        }
+        const double da = BRANCH_FREE ? orand::u01_f64_nb(w.x, w.y) : orand::u01_f64_general(w.x, w.y);
+        const double db = BRANCH_FREE ? orand::u01_f64_nb(w.z, w.w) : orand::u01_f64_general(w.z, w.w);
         const unsigned long long a = __double_as_longlong(da);
         const unsigned long long b = __double_as_longlong(db);
         return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));

@@ -90,6 +90,31 @@ def test_uniform_maps_exact(torch_cuda, orc):
     assert np.array_equal(got, w2)
 
 
+def test_f64_map_every_leading_bit(torch_cuda, orc):
+    """The FP64 map takes a short path when the high word is >= 2^20 and the
+    general one otherwise, chosen per pair of values.  Every position of the
+    high word's leading bit (and a zero high word), with random low words,
+    each paired with a partner from both paths, is bit-exact."""
+    torch = torch_cuda
+    rng = np.random.default_rng(4)
+    his = [0]
+    for p in range(32):
+        his += [int(v) | (1 << p) for v in rng.integers(0, 1 << p, 64, dtype=np.uint64)] if p else [1] * 64
+    his = np.array(his, np.uint64).astype(np.uint32)
+    n = his.size
+    partner = np.where(np.arange(n) % 2 == 0, rng.integers(1 << 20, 2**32, n, dtype=np.uint64),
+                       rng.integers(0, 1 << 20, n, dtype=np.uint64)).astype(np.uint32)
+    w = np.empty((n, 4), np.uint32)
+    w[:, 0], w[:, 2] = his, partner
+    w[:, 1] = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    w[:, 3] = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    w[::3, 1] = 0x7FF                                             # the bits the >> 11 drops
+    w[1::3, 1] = 0xFFFFF800
+    for words in (w.ravel(), w[:, [2, 3, 0, 1]].ravel()):       # each word in both slots
+        got = to_numpy(orand.map_words(W.F64_UNIFORM, torch.from_numpy(words.view(np.int32)).cuda()))
+        assert np.array_equal(got, orc.map_words(W.F64_UNIFORM, words))
+
+
 def test_map_words_odd_counts_match_fill(torch_cuda, orc):
     torch = torch_cuda
     for dtype in range(4):
