@@ -93,6 +93,16 @@ orand_status_t orand_fill_normal_f32(orand_gen_t gen, uint64_t seed, uint32_t co
 /* The same four fills selected by dtype; out is typed by dtype. */
 orand_status_t orand_fill(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, uint32_t counter,
                           uint64_t n_streams, uint64_t draws_per_stream, void *out, cudaStream_t stream);
+/* A range of a larger fill: streams first_stream .. first_stream + n_streams
+ * - 1 of the problem keyed by seed (stream g has key64 = seed ^ g), written
+ * to out[(g - first_stream) * draws_per_stream + j].  orand_fill is this
+ * call with first_stream = 0.  Disjoint ranges, on one GPU or one per rank
+ * (§3: every stream is independent), concatenate to the whole fill.
+ * Errors: as orand_fill, plus ORAND_ERR_OVERFLOW when first_stream +
+ * n_streams (or that times draws_per_stream) passes 2^64. */
+orand_status_t orand_fill_streams(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, uint32_t counter,
+                                  uint64_t first_stream, uint64_t n_streams, uint64_t draws_per_stream, void *out,
+                                  cudaStream_t stream);
 
 /* The word -> value maps alone, applied to caller-provided generator words
  * (Fig. 1's draw helpers and the Box-Muller normal map): value j of `dtype` from
@@ -105,6 +115,28 @@ orand_status_t orand_fill(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, u
  * Errors: INVALID_ARG, OVERFLOW, ALIGNMENT, CUDA. */
 orand_status_t orand_map_words(orand_dtype_t dtype, const uint32_t *words, uint64_t n_values, void *out,
                                cudaStream_t stream);
+
+/* The device header's per-thread draw interface (include/orand_device.cuh,
+ * the engine classes orand::Philox, Threefry, Squares, Tyche), run on the
+ * GPU.  It follows Fig. 1 of the paper: each thread builds its generator in
+ * registers from (its key, counter) and draws in order (§3).  Thread t
+ * builds the engine for key seed ^ t and `counter`, starting at word
+ * first_word of the stream (first_word must be 0 for Tyche, which is
+ * sequential), and runs n_rounds rounds of six draws in this order:
+ *     w  = g();               d1 = g.uniform_f64();   n  = g.normal2_f32();
+ *     u  = g.uniform_f32();   d2 = g.uniform2_f64();  u2 = g.uniform2_f32();
+ * which take 12 words per round, so draws straddle the 4-word blocks of
+ * Philox and Threefry.  Round r of thread t is a 48-byte record at
+ * out + 48 (t n_rounds + r):
+ *     double2 d2; double d1; float2 n; float2 u2; uint32_t w; float u;
+ * out: device memory, 16-byte aligned, caller-owned.  The random-access
+ * engines count words modulo 2^32 (a stream's period, §3); Tyche's draws
+ * must stay within 2^32 words.
+ * Errors: INVALID_ARG (unknown gen, NULL out with work, first_word != 0 for
+ * Tyche), OVERFLOW (size product, or more than 2^32 Tyche words per thread),
+ * ALIGNMENT, CUDA. */
+orand_status_t orand_engine_draws(orand_gen_t gen, uint64_t seed, uint32_t counter, uint32_t first_word,
+                                  uint64_t n_threads, uint32_t n_rounds, void *out, cudaStream_t stream);
 
 
 /* ------------------------------------------------------------------------
@@ -252,7 +284,8 @@ orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
  * anything is launched.
  * The first call on a device looks up that array's device address (once
  * per device, with that device current).  Make that first call before any
- * stream capture on the device.
+ * stream capture on the device.  A failed lookup is not remembered: the
+ * call returns ORAND_ERR_CUDA and the next call on that device tries again.
  * All calls share the one array.  Every slot a call reads is written
  * earlier in the same call, so nothing needs clearing between calls.  But
  * calls that run at the same time on the GPU (other streams or threads)

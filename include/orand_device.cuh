@@ -25,7 +25,8 @@
  *             d = 1367130551 ^ counter, 20 MIX; word w = b after MIX w+1.
  *
  * Maps: FP32 uniform (w >> 8) * 2^-24; FP64 uniform from two words, first
- * one high (Fig. 3), ((hi:lo) >> 11) * 2^-53, built with integer ops only;
+ * one high (Fig. 3), ((hi:lo) >> 11) * 2^-53, built with integer ops and
+ * one FP32 conversion (no FP64 arithmetic);
  * Box-Muller with u1 = ((w0>>8)+1) * 2^-24, u2 = (w1>>8) * 2^-24,
  * r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2), using the library's own
  * reduced-range log and sincospi (within 3 ulp of the FP64 values).  The
@@ -264,12 +265,12 @@ __device__ __forceinline__ float u01_f32(uint32_t w)
     return __uint2float_rn(w >> 8) * 0x1p-24f;
 }
 
-/* ((hi:lo) >> 11) * 2^-53, exact, in [0, 1).  Built from 32-bit integer ops
- * (leading-zero count, funnel shifts, exponent insert) rather than an
- * integer-to-FP64 conversion, which would run on the narrow FP64 pipe.
- * The branch on mh == 0 (probability 2^-21) is almost never taken, which is
- * cheapest for throughput-bound kernels. */
-__device__ __forceinline__ double u01_f64(uint32_t hi, uint32_t lo)
+/* ((hi:lo) >> 11) * 2^-53, exact, in [0, 1), for every (hi, lo).  Built from
+ * 32-bit integer ops (leading-zero count, funnel shifts, exponent insert)
+ * rather than an integer-to-FP64 conversion, which would run on the narrow
+ * FP64 pipe.  The branch on mh == 0 (probability 2^-21) is almost never
+ * taken.  u01_f64 below uses a shorter form for the common case. */
+__device__ __forceinline__ double u01_f64_general(uint32_t hi, uint32_t lo)
 {
     const uint32_t mh = hi >> 11;                        /* m = mh:ml, 53 bits */
     const uint32_t ml = (hi << 21) | (lo >> 11);
@@ -291,6 +292,35 @@ __device__ __forceinline__ double u01_f64(uint32_t hi, uint32_t lo)
         rl = 0u;
     }
     return __hiloint2double((int)rh, (int)rl);
+}
+
+/* The FP64 bits (high word, low word) of ((hi:lo) >> 11) * 2^-53 when
+ * hi >= 2^20 (all but 2^-12 of the words).  Let p >= 20 be the position of
+ * hi's leading bit.  hi converted to FP32 with truncation (exact in its top
+ * 24 bits) has the bit pattern ((127 + p) << 23) | (hi's 23 bits below the
+ * leading one).  The value's leading bit is 2^(p - 32), so its FP64 high word
+ * is ((991 + p) << 20) | (hi's 20 bits below the leading one): the FP32
+ * pattern shifted right by 3, plus 864 << 20.  The low word holds the next
+ * 32 bits of the 53-bit value: (hi:lo) with lo's low 11 bits (the ones the
+ * >> 11 drops) cleared, shifted right by p - 20 (0 .. 11), whose low word
+ * is one funnel shift.  Four integer operations and one conversion, against
+ * about twice that for the general form. */
+__device__ __forceinline__ uint2 u01_f64_bits_hi20(uint32_t hi, uint32_t lo)
+{
+    const uint32_t f = __float_as_uint(__uint2float_rz(hi));
+    const uint32_t sh = (f >> 23) - 147u;                       /* p - 20 */
+    return make_uint2((f >> 3) + (864u << 20), __funnelshift_r(lo & 0xFFFFF800u, hi, sh));
+}
+
+/* ((hi:lo) >> 11) * 2^-53, exact, in [0, 1), for every (hi, lo): the short
+ * form above for hi >= 2^20, the general one otherwise. */
+__device__ __forceinline__ double u01_f64(uint32_t hi, uint32_t lo)
+{
+    if (__builtin_expect(hi >= (1u << 20), 1)) {
+        const uint2 b = u01_f64_bits_hi20(hi, lo);
+        return __hiloint2double((int)b.x, (int)b.y);
+    }
+    return u01_f64_general(hi, lo);
 }
 
 /* The same map without branches (selects only), for latency-bound code
@@ -500,73 +530,110 @@ __device__ __forceinline__ float box_muller_cos_walk_f32(uint32_t w0, uint32_t w
 
 /* ------------------------------------------------ engine-style generators */
 
-/* Sequential draw interface of the paper's API (§3): construct from
- * (seed, counter), then draw words and values in order.  The random-access
- * generators keep a 4-word buffer; Tyche keeps its 4-word state. */
-class Philox {
+/* Sequential draw interface of the paper's API (§3; Fig. 1 builds
+ * `RNG rng(p.pid, counter)` in the thread and calls `draw_double2()`):
+ * construct from (seed, counter), then draw words and values in order.
+ *
+ * Every class has the same draws, each taking its words from the front of
+ * the stream: operator() one word; uniform_f32 one word; uniform_f64 two
+ * words (first one high); normal2_f32 two words (one Box-Muller pair, the
+ * fills' map); uniform2_f32 and uniform2_f64 two draws of the single form.
+ * So a thread's values are those a bulk fill of the same stream writes, in
+ * the order drawn.
+ *
+ * Period: a stream holds 2^32 words (§3).  The random-access engines count
+ * words in 32 bits, so past word 2^32 - 1 they wrap to word 0 of the same
+ * stream; they also start at any word (`first_word`, a skip-ahead).  Tyche
+ * is sequential: it starts at word 0 and does not wrap (past 2^32 words its
+ * state simply runs on); drawing that many from one stream is outside the
+ * paper's contract. */
+template <class G>
+class EngineDraws {
   public:
-    ORAND_HD Philox(uint64_t seed, uint32_t counter)
-        : key_(seed), counter_(counter), blk_(0), lane_(4) {}
+    __device__ __forceinline__ float uniform_f32() { return u01_f32(self()()); }
+    __device__ __forceinline__ double uniform_f64()
+    {
+        const uint32_t h = self()();
+        return u01_f64(h, self()());
+    }
+    __device__ __forceinline__ float2 uniform2_f32()
+    {
+        const float a = uniform_f32();
+        return make_float2(a, uniform_f32());
+    }
+    __device__ __forceinline__ double2 uniform2_f64()
+    {
+        const double a = uniform_f64();
+        return make_double2(a, uniform_f64());
+    }
+    __device__ __forceinline__ float2 normal2_f32()
+    {
+        const uint32_t a = self()();
+        return box_muller_f32(a, self()());
+    }
+
+  private:
+    ORAND_HD G &self() { return *static_cast<G *>(this); }
+};
+
+/* Philox and Threefry: word w of the stream is lane w mod 4 of the block
+ * with counter (w div 4, counter, 0, 0); a 4-word buffer holds the current
+ * block. */
+template <class BlockFn>
+class BlockEngine : public EngineDraws<BlockEngine<BlockFn>> {
+  public:
+    ORAND_HD BlockEngine(uint64_t seed, uint32_t counter, uint32_t first_word = 0)
+        : key_(seed), counter_(counter), pos_(first_word)
+    {
+        if (pos_ & 3u) buf_ = BlockFn::block(key_, counter_, pos_ >> 2);
+    }
     ORAND_HD uint32_t operator()()
     {
-        if (lane_ == 4) { buf_ = philox_block(key_, counter_, blk_++); lane_ = 0; }
-        const uint32_t w = lane_ == 0 ? buf_.x : lane_ == 1 ? buf_.y : lane_ == 2 ? buf_.z : buf_.w;
-        ++lane_;
-        return w;
+        const uint32_t lane = pos_ & 3u;
+        if (lane == 0u) buf_ = BlockFn::block(key_, counter_, pos_ >> 2);
+        ++pos_;
+        return lane == 0u ? buf_.x : lane == 1u ? buf_.y : lane == 2u ? buf_.z : buf_.w;
     }
-    __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
-    __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
-    __device__ __forceinline__ float2 uniform2_f32() { float a = uniform_f32(); return make_float2(a, uniform_f32()); }
-    __device__ __forceinline__ double2 uniform2_f64() { double a = uniform_f64(); return make_double2(a, uniform_f64()); }
-    __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
+    /* Index of the next word within the stream. */
+    ORAND_HD uint32_t position() const { return pos_; }
 
   private:
     uint64_t key_;
-    uint32_t counter_, blk_, lane_;
-    uint4 buf_;
+    uint32_t counter_, pos_;
+    uint4 buf_ = {0u, 0u, 0u, 0u};
 };
 
-class Threefry {
-  public:
-    ORAND_HD Threefry(uint64_t seed, uint32_t counter)
-        : key_(seed), counter_(counter), blk_(0), lane_(4) {}
-    ORAND_HD uint32_t operator()()
+struct PhiloxBlockFn {
+    ORAND_HD static uint4 block(uint64_t key64, uint32_t counter, uint32_t b) { return philox_block(key64, counter, b); }
+};
+struct ThreefryBlockFn {
+    ORAND_HD static uint4 block(uint64_t key64, uint32_t counter, uint32_t b)
     {
-        if (lane_ == 4) { buf_ = threefry_block(key_, counter_, blk_++); lane_ = 0; }
-        const uint32_t w = lane_ == 0 ? buf_.x : lane_ == 1 ? buf_.y : lane_ == 2 ? buf_.z : buf_.w;
-        ++lane_;
-        return w;
+        return threefry_block(key64, counter, b);
     }
-    __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
-    __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
-    __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
+};
+
+using Philox = BlockEngine<PhiloxBlockFn>;
+using Threefry = BlockEngine<ThreefryBlockFn>;
+
+/* Squares: word w = squares32((counter << 32) | w, fmix64(seed) | 1). */
+class Squares : public EngineDraws<Squares> {
+  public:
+    ORAND_HD Squares(uint64_t seed, uint32_t counter, uint32_t first_word = 0)
+        : key_(squares_key(seed)), counter_(counter), pos_(first_word) {}
+    ORAND_HD uint32_t operator()() { return squares32(((uint64_t)counter_ << 32) | pos_++, key_); }
+    ORAND_HD uint32_t position() const { return pos_; }
 
   private:
     uint64_t key_;
-    uint32_t counter_, blk_, lane_;
-    uint4 buf_;
+    uint32_t counter_, pos_;
 };
 
-class Squares {
-  public:
-    ORAND_HD Squares(uint64_t seed, uint32_t counter)
-        : key_(squares_key(seed)), ctr_((uint64_t)counter << 32) {}
-    ORAND_HD uint32_t operator()() { return squares32(ctr_++, key_); }
-    __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
-    __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
-    __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
-
-  private:
-    uint64_t key_, ctr_;
-};
-
-class Tyche {
+/* Tyche: 20 MIX from (seed, counter), then word w = b after MIX w + 1. */
+class Tyche : public EngineDraws<Tyche> {
   public:
     ORAND_HD Tyche(uint64_t seed, uint32_t counter) : s_(tyche_init(seed, counter)) {}
     ORAND_HD uint32_t operator()() { return tyche_next(s_); }
-    __device__ __forceinline__ float uniform_f32() { return u01_f32((*this)()); }
-    __device__ __forceinline__ double uniform_f64() { uint32_t h = (*this)(); return u01_f64(h, (*this)()); }
-    __device__ __forceinline__ float2 normal2_f32() { uint32_t a = (*this)(); return box_muller_f32(a, (*this)()); }
 
   private:
     TycheState s_;

@@ -28,6 +28,17 @@ extern "C" {
 orand_status_t orand_host_fill_u32(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                                    uint64_t draws_per_stream, uint32_t *out);
 
+/* n words of one stream (key seed, counter `counter`) drawn on the host
+ * through the device header's engine classes, starting at word first_word:
+ * out[i] = word (first_word + i) mod 2^32 for the random-access generators,
+ * which wrap at their 2^32-word period (§3).  Tyche is sequential:
+ * first_word must be 0 and n at most 2^32.  out: host memory, 4-byte
+ * aligned.
+ * Errors: INVALID_ARG (unknown gen, NULL out with n > 0, first_word != 0
+ * for Tyche), OVERFLOW (Tyche past 2^32 words), ALIGNMENT. */
+orand_status_t orand_host_engine_words(orand_gen_t gen, uint64_t seed, uint32_t counter, uint32_t first_word,
+                                       uint64_t n, uint32_t *out);
+
 /* The micro-benchmark.  For each lengths[k] (1..2^32), construct fresh
  * generators (seed r = 0, 1, 2, ..., counter 0; std::mt19937 seeded with r
  * for gen = ORAND_HOST_MT19937) and draw lengths[k] words from each, about

@@ -50,11 +50,14 @@ _SIGS = {
     "orand_version": (_i32, []),
     "orand_last_cuda_error": (_i32, []),
     "orand_fill": (_i32, [_i32, _i32, _u64, _u32, _u64, _u64, _vp, _vp]),
+    "orand_fill_streams": (_i32, [_i32, _i32, _u64, _u32, _u64, _u64, _u64, _vp, _vp]),
     "orand_fill_u32": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
     "orand_fill_uniform_f32": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
     "orand_fill_uniform_f64": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
     "orand_fill_normal_f32": (_i32, [_i32, _u64, _u32, _u64, _u64, _vp, _vp]),
     "orand_map_words": (_i32, [_i32, _vp, _u64, _vp, _vp]),
+    "orand_engine_draws": (_i32, [_i32, _u64, _u32, _u32, _u64, _u32, _vp, _vp]),
+    "orand_host_engine_words": (_i32, [_i32, _u64, _u32, _u32, _u64, _vp]),
     "orand_ctx_create": (_i32, [ctypes.POINTER(_vp)]),
     "orand_ctx_destroy": (_i32, [_vp]),
     "orand_brownian_walk": (_i32, [_vp, _vp, _vp]),
@@ -195,6 +198,12 @@ def orand_fill(gen, dtype, seed, counter, n_streams, draws_per_stream, out_ptr, 
                              draws_per_stream, out_ptr, stream_handle), "orand_fill")
 
 
+def orand_fill_streams(gen, dtype, seed, counter, first_stream, n_streams, draws_per_stream, out_ptr,
+                       stream_handle):
+    _check(_lib().orand_fill_streams(gen, dtype, seed & (2**64 - 1), counter & 0xFFFFFFFF, first_stream,
+                                     n_streams, draws_per_stream, out_ptr, stream_handle), "orand_fill_streams")
+
+
 def orand_fill_u32(gen, seed, counter, n_streams, draws_per_stream, out_ptr, stream_handle):
     _check(_lib().orand_fill_u32(gen, seed & (2**64 - 1), counter & 0xFFFFFFFF, n_streams, draws_per_stream,
                                  out_ptr, stream_handle), "orand_fill_u32")
@@ -241,8 +250,10 @@ def map_words(dtype: int, words, n_values=None, stream=None):
 
 
 def fill(gen: int, dtype: int, seed: int, counter: int, n_streams: int, draws_per_stream: int, out=None,
-         device="cuda", stream=None):
-    """Bulk fill into a (new or given) CUDA tensor of n_streams*draws_per_stream values."""
+         device="cuda", stream=None, first_stream: int = 0):
+    """Bulk fill into a (new or given) CUDA tensor of n_streams*draws_per_stream
+    values: streams first_stream .. first_stream + n_streams - 1 of the fill
+    keyed by seed."""
     import torch
 
     n = n_streams * draws_per_stream
@@ -250,8 +261,47 @@ def fill(gen: int, dtype: int, seed: int, counter: int, n_streams: int, draws_pe
         out = torch.empty(n, dtype=torch_dtype(dtype), device=device)
     if out.numel() < n or not out.is_cuda or not out.is_contiguous():
         raise ValueError("out must be a contiguous CUDA tensor with at least %d elements" % n)
-    orand_fill(gen, dtype, seed, counter, n_streams, draws_per_stream, _ptr(out) if n else 0,
-               _stream_handle(stream))
+    if first_stream:
+        orand_fill_streams(gen, dtype, seed, counter, first_stream, n_streams, draws_per_stream,
+                           _ptr(out) if n else 0, _stream_handle(stream))
+    else:
+        orand_fill(gen, dtype, seed, counter, n_streams, draws_per_stream, _ptr(out) if n else 0,
+                   _stream_handle(stream))
+    return out
+
+
+# ------------------------------------------------- per-thread engines --
+
+# One round of orand_engine_draws (48 bytes): the draws in the order
+# w, d1, n, u, d2, u2; stored d2, d1, n, u2, w, u.
+ENGINE_RECORD_FIELDS = [("d2", "<f8", (2,)), ("d1", "<f8"), ("n", "<f4", (2,)), ("u2", "<f4", (2,)),
+                        ("w", "<u4"), ("u", "<f4")]
+ENGINE_RECORD_BYTES = 48
+
+
+def orand_engine_draws(gen, seed, counter, first_word, n_threads, n_rounds, out_ptr, stream_handle):
+    _check(_lib().orand_engine_draws(gen, seed & (2**64 - 1), counter & 0xFFFFFFFF, first_word & 0xFFFFFFFF,
+                                     n_threads, n_rounds, out_ptr, stream_handle), "orand_engine_draws")
+
+
+def engine_draws(gen, seed, counter, n_threads, n_rounds, first_word=0, stream=None):
+    """Per-thread draws through the device header's engine classes: a CUDA
+    uint8 tensor of n_threads * n_rounds 48-byte records (ENGINE_RECORD_FIELDS)."""
+    import torch
+
+    out = torch.empty(max(n_threads * n_rounds * ENGINE_RECORD_BYTES, 16), dtype=torch.uint8, device="cuda")
+    orand_engine_draws(gen, seed, counter, first_word, n_threads, n_rounds, _ptr(out), _stream_handle(stream))
+    return out
+
+
+def host_engine_words(gen, seed, counter, n, first_word=0):
+    """n words of one stream drawn on the host through the engine classes,
+    from word first_word (numpy uint32)."""
+    import numpy as np
+
+    out = np.empty(n, dtype=np.uint32)
+    _check(_lib().orand_host_engine_words(gen, seed & (2**64 - 1), counter & 0xFFFFFFFF, first_word & 0xFFFFFFFF,
+                                          n, out.ctypes.data if n else None), "orand_host_engine_words")
     return out
 
 
@@ -535,24 +585,27 @@ def _autograd_function():
         """loss = BrownianWalk3D.apply(mu, sigma, x0, steps, dt, k, seed, ckpt_every, kappa)
 
         Forward runs the fused walk with drift mu - kappa x.  It writes
-        checkpoints every `ckpt_every` steps (kept for backward and exposed as
-        `last_checkpoints`).  Backward runs the adjoint kernel, which
-        regenerates every noise draw from its (particle, step) key instead of
-        storing it; for kappa it recomputes positions backwards from the
-        checkpoints.  mu: (3,) tensor; sigma and kappa: 0-dim tensors (each
-        may require grad; kappa may be None for 0); x0: (n, 3) CUDA float32.
-        """
+        checkpoints every `ckpt_every` steps; they are saved for backward on
+        this call's autograd context only, so they are freed with the graph
+        once backward has run (call walk3d_forward directly to keep them).
+        Backward runs the adjoint kernel, which regenerates every noise draw
+        from its (particle, step) key instead of storing it; for kappa it
+        recomputes positions backwards from the checkpoints.
 
-        last_checkpoints = None
+        mu: (3,) tensor; sigma and kappa: 0-dim tensors (each may require
+        grad; kappa may be None for 0); x0: (n, 3) CUDA float32.  mu, sigma
+        and kappa enter the kernels by value, as kernel parameters: keep
+        them on the CPU (their gradients come back on the CPU too), since
+        reading a CUDA tensor's value waits for the device.
+        """
 
         @staticmethod
         def forward(ctx, mu, sigma, x0, steps, dt=1e-3, k=2.0, seed=0, ckpt_every=64, kappa=None):
-            mu_v = [float(v) for v in mu.detach().cpu().tolist()]
-            kap = 0.0 if kappa is None else float(kappa.detach().cpu())
-            p = walk3d_params(x0.shape[0], int(steps), float(dt), mu_v, float(sigma.detach().cpu()), float(k),
+            mu_v = [float(v) for v in mu.detach().reshape(-1).tolist()]
+            kap = 0.0 if kappa is None else float(kappa.detach())
+            p = walk3d_params(x0.shape[0], int(steps), float(dt), mu_v, float(sigma.detach()), float(k),
                               int(seed), int(ckpt_every), kappa=kap)
             xT, ckpt, loss = walk3d_forward(p, x0=x0, want_ckpt=bool(ckpt_every))
-            BrownianWalk3D.last_checkpoints = ckpt
             ctx.params = p
             ctx.want_dkappa = kappa is not None and kappa.requires_grad
             ctx.meta = [(t.dtype, t.device) if t is not None else None for t in (mu, sigma, kappa)]

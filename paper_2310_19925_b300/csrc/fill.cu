@@ -1,6 +1,7 @@
 // Bulk fill kernels: n_streams x draws_per_stream values, stream-major,
 // stream s keyed by seed ^ s (one stream per processing element, §3 of the
-// paper).  Write-only and HBM-bound for Philox; integer-pipe-bound for the
+// paper); a call may start at any global stream (first_stream), so ranks or
+// chunks of one problem fill disjoint stream ranges of it.  Write-only and HBM-bound for Philox; integer-pipe-bound for the
 // longer round functions.
 //
 // Work unit: a "group" of four consecutive generator words of one stream
@@ -23,6 +24,7 @@ namespace orand_impl {
 
 struct FillArgs {
     uint64_t seed;
+    uint64_t s_first;     // global index of stream 0 of this call
     uint64_t n_streams;
     uint64_t dps;         // values per stream
     uint64_t n_groups;    // n_streams * G
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(256) fill_random_access_kernel(FillArgs a)
     uint64_t s = g / a.G;
     uint32_t b = (uint32_t)(g - s * a.G);
     for (;;) {
-        const uint4 w = group_words<GEN>(a.seed ^ s, a.counter, b);
+        const uint4 w = group_words<GEN>(a.seed ^ (a.s_first + s), a.counter, b);
         store_group<DT, VEC>(a.out, g, s, b, a.dps, w);
         g += stride;
         if (g >= a.n_groups) break;
@@ -107,7 +109,7 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v)
 
 struct TileArgs {
     uint64_t seed;
-    uint64_t r_first;      // global index of this launch's first run
+    uint64_t r_first;      // global index of this launch's first run (the call's first stream x runs per stream, plus the runs of earlier launches)
     uint64_t n_runs;       // runs of this launch
     uint64_t n_tiles;      // ceil(n_runs / (T * TR))
     uint64_t full_chunks;  // 16-byte chunks in the full 128-byte rows of this launch's output
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(256) fill_tyche_kernel(FillArgs a)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_streams; s += stride) {
-        orand::TycheState st = orand::tyche_init(a.seed ^ s, a.counter);
+        orand::TycheState st = orand::tyche_init(a.seed ^ (a.s_first + s), a.counter);
         for (uint32_t b = 0; b < a.G; ++b) {
             uint4 w;
             w.x = orand::tyche_next(st);
@@ -323,7 +325,7 @@ static orand_status_t launch_tile_shape(TileArgs a, const DeviceInfo &info, cuda
     uint4 *const out0 = a.out;
     for (uint64_t r0 = 0; r0 < total_runs; r0 += runs_per_launch) {
         TileArgs p = a;
-        p.r_first = r0;
+        p.r_first = a.r_first + r0;
         // The last launch takes a remainder of less than one row as well, so
         // every launch has at least one full row.
         const uint64_t left = total_runs - r0;
@@ -423,17 +425,19 @@ static bool stream_words(int dt, uint64_t dps, uint64_t *words)
     return true;
 }
 
-orand_status_t fill_validate(int gen, int dt, uint64_t n_streams, uint64_t dps, const void *out,
+orand_status_t fill_validate(int gen, int dt, uint64_t s_first, uint64_t n_streams, uint64_t dps, const void *out,
                              uint64_t *n_values)
 {
     if (gen < 0 || gen > 3 || dt < 0 || dt > 3) return ORAND_ERR_INVALID_ARG;
-    uint64_t n, bytes, words;
+    uint64_t n, bytes, words, run_end;
     if (mul_overflows(n_streams, dps, &n)) return ORAND_ERR_OVERFLOW;
     const uint64_t elem = dt == ORAND_F64_UNIFORM ? 8 : 4;
     if (mul_overflows(n, elem, &bytes)) return ORAND_ERR_OVERFLOW;
     if (!stream_words(dt, dps, &words) || words > (1ull << 32)) return ORAND_ERR_OVERFLOW;
     *n_values = n;
     if (n == 0) return ORAND_OK;
+    if (s_first > UINT64_MAX - n_streams) return ORAND_ERR_OVERFLOW;      // global stream ids stay below 2^64
+    if (mul_overflows(s_first + n_streams, dps, &run_end)) return ORAND_ERR_OVERFLOW;
     if (out == nullptr) return ORAND_ERR_INVALID_ARG;
     if ((uintptr_t)out % elem) return ORAND_ERR_ALIGNMENT;
     return ORAND_OK;
@@ -449,11 +453,11 @@ static bool tile_path_disabled()
     return off;
 }
 
-orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uint64_t n_streams, uint64_t dps,
-                           void *out, cudaStream_t stream)
+orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uint64_t s_first, uint64_t n_streams,
+                           uint64_t dps, void *out, cudaStream_t stream)
 {
     uint64_t n = 0;
-    orand_status_t st = fill_validate(gen, dt, n_streams, dps, out, &n);
+    orand_status_t st = fill_validate(gen, dt, s_first, n_streams, dps, out, &n);
     if (st != ORAND_OK || n == 0) return st;
     DeviceInfo info;
     if ((st = current_device(&info)) != ORAND_OK) return st;
@@ -473,7 +477,7 @@ orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uin
             t.counter = counter;
             t.rps = G / R;
             t.n_runs = n_streams * t.rps;
-            t.r_first = 0;
+            t.r_first = s_first * t.rps;   // no overflow: (s_first + n_streams) * dps was checked
             t.n_tiles = 0;      // set per launch
             t.full_chunks = 0;  // set per launch
             t.rps_shift = (t.rps & (t.rps - 1)) == 0 ? __builtin_ctzll(t.rps) : -1;
@@ -488,6 +492,7 @@ orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uin
     }
     FillArgs a;
     a.seed = seed;
+    a.s_first = s_first;
     a.counter = counter;
     a.n_streams = n_streams;
     a.dps = dps;
@@ -574,34 +579,42 @@ orand_status_t orand_map_words(orand_dtype_t dtype, const uint32_t *words, uint6
 orand_status_t orand_fill(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, uint32_t counter,
                           uint64_t n_streams, uint64_t draws_per_stream, void *out, cudaStream_t stream)
 {
-    return orand_impl::fill_launch((int)gen, (int)dtype, seed, counter, n_streams, draws_per_stream, out,
+    return orand_impl::fill_launch((int)gen, (int)dtype, seed, counter, 0, n_streams, draws_per_stream, out,
                                    stream);
+}
+
+orand_status_t orand_fill_streams(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, uint32_t counter,
+                                  uint64_t first_stream, uint64_t n_streams, uint64_t draws_per_stream, void *out,
+                                  cudaStream_t stream)
+{
+    return orand_impl::fill_launch((int)gen, (int)dtype, seed, counter, first_stream, n_streams, draws_per_stream,
+                                   out, stream);
 }
 
 orand_status_t orand_fill_u32(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                               uint64_t draws_per_stream, uint32_t *out, cudaStream_t stream)
 {
-    return orand_impl::fill_launch((int)gen, ORAND_U32, seed, counter, n_streams, draws_per_stream, out, stream);
+    return orand_impl::fill_launch((int)gen, ORAND_U32, seed, counter, 0, n_streams, draws_per_stream, out, stream);
 }
 
 orand_status_t orand_fill_uniform_f32(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                                       uint64_t draws_per_stream, float *out, cudaStream_t stream)
 {
-    return orand_impl::fill_launch((int)gen, ORAND_F32_UNIFORM, seed, counter, n_streams, draws_per_stream,
+    return orand_impl::fill_launch((int)gen, ORAND_F32_UNIFORM, seed, counter, 0, n_streams, draws_per_stream,
                                    out, stream);
 }
 
 orand_status_t orand_fill_uniform_f64(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                                       uint64_t draws_per_stream, double *out, cudaStream_t stream)
 {
-    return orand_impl::fill_launch((int)gen, ORAND_F64_UNIFORM, seed, counter, n_streams, draws_per_stream,
+    return orand_impl::fill_launch((int)gen, ORAND_F64_UNIFORM, seed, counter, 0, n_streams, draws_per_stream,
                                    out, stream);
 }
 
 orand_status_t orand_fill_normal_f32(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                                      uint64_t draws_per_stream, float *out, cudaStream_t stream)
 {
-    return orand_impl::fill_launch((int)gen, ORAND_F32_NORMAL, seed, counter, n_streams, draws_per_stream,
+    return orand_impl::fill_launch((int)gen, ORAND_F32_NORMAL, seed, counter, 0, n_streams, draws_per_stream,
                                    out, stream);
 }
 

@@ -44,6 +44,40 @@ double time_streams(Make make, uint64_t len, uint64_t reps, uint32_t *acc)
 
 extern "C" {
 
+orand_status_t orand_host_engine_words(orand_gen_t gen, uint64_t seed, uint32_t counter, uint32_t first_word,
+                                       uint64_t n, uint32_t *out)
+{
+    if ((unsigned)gen > ORAND_TYCHE) return ORAND_ERR_INVALID_ARG;
+    if (gen == ORAND_TYCHE && first_word != 0) return ORAND_ERR_INVALID_ARG;
+    if (gen == ORAND_TYCHE && n > (1ull << 32)) return ORAND_ERR_OVERFLOW;
+    if (n == 0) return ORAND_OK;
+    if (out == nullptr) return ORAND_ERR_INVALID_ARG;
+    if ((uintptr_t)out % 4) return ORAND_ERR_ALIGNMENT;
+    switch (gen) {
+    case ORAND_PHILOX4x32_10: {
+        orand::Philox e(seed, counter, first_word);
+        for (uint64_t i = 0; i < n; ++i) out[i] = e();
+        break;
+    }
+    case ORAND_THREEFRY4x32_20: {
+        orand::Threefry e(seed, counter, first_word);
+        for (uint64_t i = 0; i < n; ++i) out[i] = e();
+        break;
+    }
+    case ORAND_SQUARES32: {
+        orand::Squares e(seed, counter, first_word);
+        for (uint64_t i = 0; i < n; ++i) out[i] = e();
+        break;
+    }
+    default: {
+        orand::Tyche e(seed, counter);
+        for (uint64_t i = 0; i < n; ++i) out[i] = e();
+        break;
+    }
+    }
+    return ORAND_OK;
+}
+
 orand_status_t orand_host_fill_u32(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                                    uint64_t draws_per_stream, uint32_t *out)
 {

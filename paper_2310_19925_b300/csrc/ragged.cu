@@ -763,8 +763,8 @@ orand_status_t ragged_serve(orand_ctx_t ctx, const orand_request_t *reqs, size_t
     return ORAND_OK;
 }
 
-orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uint64_t n_streams, uint64_t dps,
-                           void *out, cudaStream_t stream);
+orand_status_t fill_launch(int gen, int dt, uint64_t seed, uint32_t counter, uint64_t s_first, uint64_t n_streams,
+                           uint64_t dps, void *out, cudaStream_t stream);
 
 }  // namespace orand_impl
 
@@ -790,7 +790,7 @@ orand_status_t orand_fill_ragged_serial(const orand_request_t *reqs, size_t n, v
     for (size_t i = 0; i < n; ++i) {
         const orand_request_t &q = reqs[i];
         if (q.length == 0) continue;
-        st = fill_launch((int)q.gen, (int)q.dtype, q.seed, q.counter, 1, q.length,
+        st = fill_launch((int)q.gen, (int)q.dtype, q.seed, q.counter, 0, 1, q.length,
                          (char *)out_base + q.out_offset_bytes, stream);
         if (st != ORAND_OK) return st;
     }

@@ -51,6 +51,12 @@ def test_bad_enums_rejected(lib, gen, dtype):
     assert lib.orand_fill(gen, dtype, 1, 0, 4, 4, 16, None) == -1
 
 
+def test_stream_range_overflow_rejected(lib):
+    assert lib.orand_fill_streams(0, 0, 1, 0, 2**64 - 10, 11, 4, 16, None) == -2   # stream ids pass 2^64
+    assert lib.orand_fill_streams(0, 0, 1, 0, 2**62, 2**62, 16, 16, None) == -2     # (first + n) * dps overflows
+    assert lib.orand_fill_streams(0, 0, 1, 0, 2**64 - 10, 0, 4, None, None) == 0    # empty range
+
+
 def test_overflow_rejected(lib):
     assert lib.orand_fill(0, 0, 1, 0, 2**40, 2**30, 16, None) == -2          # n*dps overflows
     assert lib.orand_fill(0, 0, 1, 0, 2**62, 2, 16, None) == -2              # bytes overflow

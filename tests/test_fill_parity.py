@@ -4,7 +4,7 @@ Bar: u32 words, FP32 and FP64 uniforms bit-exact; FP32 normals within 4 ulp
 (ordered-integer distance) of the FP64 oracle value rounded to FP32.  Small
 shapes span several groups, ragged tails and both store paths; the full
 2^24 x 16 workload runs in the benchmark's launch configuration and is
-checked on sampled streams plus whole-array properties.
+checked on every value, plus whole-array properties.
 """
 import math
 
@@ -127,20 +127,25 @@ def test_fill_is_independent_of_stream_range_split(torch_cuda):
 
 @pytest.mark.parametrize("gen", GENS)
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_fill_large_workload_sampled(torch_cuda, orc, gen, dtype):
-    """The benchmark's 2^24 x 16 fill, exact on sampled streams plus range and moments on all values."""
+def test_fill_large_workload_every_value(torch_cuda, orc, gen, dtype):
+    """The benchmark's 2^24 x 16 fill (2^28 values) in its launch
+    configuration, compared with the oracle on every value: the oracle runs
+    on all host threads over chunks of 2^21 streams.  Plus range and moments
+    over the whole array."""
+    import os
+
     torch = torch_cuda
     c = W.FILL_LARGE
     n_streams, dps = c["n_streams"], c["dps"]
     out = orand.fill(gen, dtype, c["seed"], c["counter"], n_streams, dps)
     torch.cuda.synchronize()
-    rng = np.random.default_rng(1000 + 4 * gen + dtype)
-    streams = np.unique(np.concatenate([[0, 1, n_streams - 1], rng.integers(0, n_streams, 1024)]))
-    idx = torch.as_tensor((streams[:, None] * dps + np.arange(dps)[None, :]).ravel(), device="cuda")
-    got = to_numpy(out[idx]).reshape(len(streams), dps)
-    for i, s in enumerate(streams):
-        ref = orc.fill(gen, dtype, c["seed"], c["counter"], 1, dps, s_first=int(s))
-        compare(dtype, got[i], ref)
+    host = to_numpy(out)
+    threads = os.cpu_count() or 1
+    chunk = 1 << 21
+    for s0 in range(0, n_streams, chunk):
+        ref = orc.fill(gen, dtype, c["seed"], c["counter"], chunk, dps, s_first=s0, threads=threads)
+        compare(dtype, host[s0 * dps:(s0 + chunk) * dps], ref)
+    del host, ref
     n = out.numel()
     if dtype == W.F32_UNIFORM:
         assert out.min().item() >= 0.0 and out.max().item() <= 1.0 - 2.0 ** -24
@@ -160,6 +165,28 @@ def test_fill_large_workload_sampled(torch_cuda, orc, gen, dtype):
         assert abs(chi2 - 255) < 5 * math.sqrt(2 * 255)
     del out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("gen", GENS)
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape", [(1000, 16), (101, 5)])
+def test_fill_stream_ranges_concatenate(torch_cuda, orc, gen, dtype, shape):
+    """orand_fill_streams: uneven, single-stream and empty ranges of one fill
+    (tiled and untiled paths) concatenate to the whole fill, and a range far
+    from stream 0 matches the oracle's streams there."""
+    torch = torch_cuda
+    n_streams, dps = shape
+    full = orand.fill(gen, dtype, 0x5EED, 3, n_streams, dps)
+    parts = torch.zeros_like(full)
+    cuts = [0, 1, n_streams // 3, n_streams // 3, n_streams - 1, n_streams]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        if b > a:
+            orand.fill(gen, dtype, 0x5EED, 3, b - a, dps, out=parts[a * dps:b * dps], first_stream=a)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_numpy(parts), to_numpy(full))
+    first = 2**40 + 12345
+    got = to_numpy(orand.fill(gen, dtype, 0x5EED, 3, 300, dps, first_stream=first))
+    compare(dtype, got, orc.fill(gen, dtype, 0x5EED, 3, 300, dps, s_first=first))
 
 
 @pytest.mark.parametrize("extra", [9, 16])
