@@ -10,6 +10,7 @@
 // integer- and FP-pipe work per step, not bytes.
 #include <math.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -873,27 +874,34 @@ constexpr unsigned kNoAllocMaxBlocks = (unsigned)(kNoAllocMaxParticles / kWalkBl
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * kRedWidth];
 
 constexpr int kNoAllocDevices = 64;
-static std::once_flag g_noalloc_once[kNoAllocDevices];
-static double *g_noalloc_ptr[kNoAllocDevices];
-static cudaError_t g_noalloc_err[kNoAllocDevices];
+static std::mutex g_noalloc_mutex[kNoAllocDevices];
+static std::atomic<double *> g_noalloc_ptr[kNoAllocDevices];
 
-// Device address of g_noalloc_partials on the current device, looked up once
-// per device (the host-side name is only a stand-in for that address).
+// Device address of g_noalloc_partials on the current device (the host-side
+// name is only a stand-in for that address).  Only a successful lookup is
+// kept: after a failure (for example a first call made inside a stream
+// capture) the next call on that device tries again.
 static orand_status_t noalloc_partials(double **out)
 {
     int dev = -1;
     ORAND_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocDevices) return ORAND_ERR_UNSUPPORTED;
-    std::call_once(g_noalloc_once[dev], [dev] {
-        void *p = nullptr;
-        g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        g_noalloc_ptr[dev] = (double *)p;
-    });
-    if (g_noalloc_err[dev] != cudaSuccess) {
-        log_cuda_failure("cudaGetSymbolAddress(g_noalloc_partials)", __FILE__, __LINE__, g_noalloc_err[dev]);
-        return cuda_status(g_noalloc_err[dev]);
+    double *ptr = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (ptr == nullptr) {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex[dev]);
+        ptr = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+        if (ptr == nullptr) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+            if (e != cudaSuccess || p == nullptr) {
+                log_cuda_failure("cudaGetSymbolAddress(g_noalloc_partials)", __FILE__, __LINE__, e);
+                return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+            }
+            ptr = (double *)p;
+            g_noalloc_ptr[dev].store(ptr, std::memory_order_release);
+        }
     }
-    *out = g_noalloc_ptr[dev];
+    *out = ptr;
     return ORAND_OK;
 }
 
