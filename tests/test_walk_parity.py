@@ -175,7 +175,6 @@ def test_walk3d_autograd_function(torch_cuda, orc):
     sigma = torch.tensor(0.5, dtype=torch.float32, requires_grad=True)
     loss = BW.apply(mu, sigma, x0, steps, 1e-3, 2.0, 0, 32)
     loss.backward()
-    assert BW.last_checkpoints.shape == (4, n, 3)
     oxT, _ = orc.walk3d_forward(0, n, steps, 32, _f32(1e-3), MU, 0.5)
     odmu, odsig, odx0 = orc.walk3d_adjoint(0, n, steps, _f32(1e-3), oxT, 2.0, n)
     assert loss.item() == pytest.approx(orc.walk3d_loss(oxT, 2.0, n), rel=1e-6)
@@ -189,6 +188,31 @@ def test_walk3d_autograd_function(torch_cuda, orc):
         lm = BW.apply(mu, sigma - h, x0, steps, 1e-3, 2.0, 0, 32).item()
     sp, sm = _f32(_f32(0.5) + h), _f32(_f32(0.5) - h)
     assert (lp - lm) / (sp - sm) == pytest.approx(sigma.grad.item(), rel=GRAD_TOL)
+
+
+def test_walk3d_autograd_frees_checkpoints_after_backward(torch_cuda):
+    """The forward's checkpoints live on the call's autograd context only:
+    held between forward and backward, freed once backward has run (what is
+    left is x0's gradient).  mu and sigma stay on the CPU, so no device read
+    is needed to set up the kernels."""
+    torch = torch_cuda
+    n, steps, K = 1 << 18, 256, 32                 # 8 checkpoints of 3 MiB each
+    BW = orand.BrownianWalk3D()
+    p = _p(n, steps, K=K)
+    x0 = orand.walk3d_init(p).requires_grad_(True)
+    mu = torch.tensor(MU, dtype=torch.float32, requires_grad=True)
+    sigma = torch.tensor(0.5, dtype=torch.float32, requires_grad=True)
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    loss = BW.apply(mu, sigma, x0, steps, 1e-3, 2.0, 0, K)
+    held = torch.cuda.memory_allocated() - base
+    assert held >= (steps // K) * n * 3 * 4         # checkpoints (and x_T) kept for backward
+    loss.backward()
+    del loss
+    torch.cuda.synchronize()
+    left = torch.cuda.memory_allocated() - base
+    assert left <= n * 3 * 4 + (1 << 16), (held, left)   # x0.grad and small scalars only
+    assert x0.grad is not None and mu.grad.device.type == "cpu"
 
 
 def test_walk3d_plain_baseline_matches_fused(torch_cuda):
