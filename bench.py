@@ -102,6 +102,25 @@ def source_hash(paths):
     return h.hexdigest()[:12]
 
 
+# Issue peak in warp-instructions/s: 148 SMs x 4 schedulers x 2.032 GHz.
+ISSUE_PEAK_WARP_INST = 148 * 4 * 2.032e9
+
+
+def fill_issue_counts(src_hash):
+    """Per (generator, dtype) of the 2^24 x 16 fill: (warp-instructions per
+    launch, busiest pipe, its % of peak) from the committed ncu summary, if it
+    was taken on the current sources of the fill kernels (else {})."""
+    p = os.path.join(ROOT, "profiles", "fill_issue_2p24x16.txt")
+    out = {}
+    if not os.path.exists(p):
+        return out
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 6 and not line.startswith("#") and parts[2] == src_hash:
+            out[(int(parts[0]), int(parts[1]))] = (float(parts[3]), parts[4], float(parts[5]))
+    return out
+
+
 def ncu_traffic(kernel_key, src_hash):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current source of the kernel (else None)."""
@@ -178,7 +197,7 @@ def fill_rows(torch, orand, W, rank):
     rows = []
     c = W.FILL_LARGE
     n_streams, dps = c["n_streams"], c["dps"]
-    seed = c["seed"] ^ (rank * n_streams)   # rank r owns global streams [r*2^24, (r+1)*2^24)
+    first = rank * n_streams                 # rank r fills global streams [r*2^24, (r+1)*2^24)
     bufs = {}
     for dt in (W.U32, W.F32_UNIFORM, W.F64_UNIFORM, W.F32_NORMAL):
         bufs[dt] = torch.empty(n_streams * dps, dtype=orand.torch_dtype(dt), device="cuda")
@@ -188,21 +207,24 @@ def fill_rows(torch, orand, W, rank):
             nbytes = out.numel() * out.element_size()
 
             def run(sh, gen=gen, dt=dt, out=out):
-                orand.orand_fill(gen, dt, seed, c["counter"], n_streams, dps, out.data_ptr(), sh)
+                orand.orand_fill_streams(gen, dt, c["seed"], c["counter"], first, n_streams, dps, out.data_ptr(), sh)
 
-            rows.append(Row("fill/%s/%s" % (W.GEN_NAMES[gen], W.DTYPE_NAMES[dt]), run, nbytes, "B", 1,
-                            bytes_written=nbytes))
+            row = Row("fill/%s/%s" % (W.GEN_NAMES[gen], W.DTYPE_NAMES[dt]), run, nbytes, "B", 1,
+                      bytes_written=nbytes)
+            row.gen, row.dtype = gen, dt
+            rows.append(row)
     # The small Philox fill (2^16 streams x 64 draws, 16 MiB per dtype): it
     # stays in the 126 MB L2, so the launch's latency is what is measured.
     cs = W.FILL_SMALL
-    s_seed = cs["seed"] ^ (rank * cs["n_streams"])
+    s_first = rank * cs["n_streams"]
     for dt in (W.U32, W.F32_UNIFORM):
         out = torch.empty(cs["n_streams"] * cs["dps"], dtype=orand.torch_dtype(dt), device="cuda")
         bufs[("small", dt)] = out
         nbytes = out.numel() * out.element_size()
 
         def run_small(sh, dt=dt, out=out):
-            orand.orand_fill(W.PHILOX, dt, s_seed, cs["counter"], cs["n_streams"], cs["dps"], out.data_ptr(), sh)
+            orand.orand_fill_streams(W.PHILOX, dt, cs["seed"], cs["counter"], s_first, cs["n_streams"], cs["dps"],
+                                     out.data_ptr(), sh)
 
         row = Row("fill_small/philox4x32_10/%s" % W.DTYPE_NAMES[dt], run_small, nbytes, "B", 1)
         row.extra = {"note": "16 MiB, L2-resident: launch latency, not HBM"}
@@ -210,8 +232,13 @@ def fill_rows(torch, orand, W, rank):
     return rows, bufs
 
 
-def walk_rows(torch, orand, W, rank):
-    """Fused 2D walk (particle-steps) and fused 3D forward + adjoint."""
+def walk_rows(torch, orand, W, rank, world):
+    """Fused 2D walk (particle-steps) and fused 3D forward + adjoint.  Rank r
+    owns particles [r P, (r+1) P); the 3D loss is normalised by the global
+    count, and with more than one rank the loss and scalar gradients are
+    summed over ranks (one all-reduce of five or six doubles per row)."""
+    from paper_2310_19925_b300 import shard
+
     rows = []
     keep = {}
     c2 = W.WALK2D
@@ -228,7 +255,7 @@ def walk_rows(torch, orand, W, rank):
     c3 = W.WALK3D
     P3, T = c3["n_particles"], c3["steps"]
     prm3 = orand.walk3d_params(P3, T, c3["dt"], c3["mu"], c3["sigma"], c3["k"], c3["seed"], c3["ckpt_every"],
-                               p_first=rank * P3, p_total=P3)
+                               p_first=rank * P3, p_total=world * P3)
     ctx = orand.default_context().handle
     xT = torch.empty((P3, 3), dtype=torch.float32, device="cuda")
     ck = torch.empty((orand.n_checkpoints(T, c3["ckpt_every"]), P3, 3), dtype=torch.float32, device="cuda")
@@ -242,6 +269,8 @@ def walk_rows(torch, orand, W, rank):
         orand.orand_walk3d_fwd(ctx, prm3, 0, xT.data_ptr(), ck.data_ptr(), loss.data_ptr(), sh)
         orand.orand_walk3d_bwd(ctx, prm3, xT.data_ptr(), ck.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(), 0,
                                dx0.data_ptr(), sh)
+        if world > 1:
+            shard.allreduce_walk_scalars(loss, dmu, dsig)
 
     rows.append(Row("walk3d/fused_fwd+adjoint", run3, P3 * T, "particle-steps", 5))
 
@@ -249,7 +278,7 @@ def walk_rows(torch, orand, W, rank):
     # backwards from the checkpoints and also returns dL/dkappa.
     co = W.WALK3D_OU
     prmo = orand.walk3d_params(P3, T, co["dt"], co["mu"], co["sigma"], co["k"], co["seed"], co["ckpt_every"],
-                               p_first=rank * P3, p_total=P3, kappa=co["kappa"])
+                               p_first=rank * P3, p_total=world * P3, kappa=co["kappa"])
     dkap = torch.empty((), dtype=torch.float64, device="cuda")
     keep["dkap"] = dkap
 
@@ -257,17 +286,25 @@ def walk_rows(torch, orand, W, rank):
         orand.orand_walk3d_fwd(ctx, prmo, 0, xT.data_ptr(), ck.data_ptr(), loss.data_ptr(), sh)
         orand.orand_walk3d_bwd(ctx, prmo, xT.data_ptr(), ck.data_ptr(), 0, dmu.data_ptr(), dsig.data_ptr(),
                                dkap.data_ptr(), dx0.data_ptr(), sh)
+        if world > 1:
+            shard.allreduce_walk_scalars(loss, dmu, dsig, dkap)
 
     rows.append(Row("walk3d/ou_fused_fwd+adjoint", run3ou, P3 * T, "particle-steps", 6))
     return rows, keep
 
 
-def ragged_rows(torch, orand, W, rank):
-    """The 100,000-request ragged batch (about 30 GB of output) as one graph-launched persistent kernel."""
+def ragged_rows(torch, orand, W, rank, world):
+    """The 100,000-request ragged batch (about 30 GB of output) as one
+    graph-launched persistent kernel.  With several ranks the list is split
+    by the sharding helper (Tyche chains spread longest first, then bytes
+    balanced), each rank serving its share into a buffer of its own."""
     import numpy as np
 
+    from paper_2310_19925_b300 import shard
+
     recs, total = W.ragged_requests()
-    recs["seed"] += np.uint64(rank * len(recs))     # rank-disjoint request seeds
+    if world > 1:
+        recs, total, _ = shard.ragged_shard(recs, rank, world)
     out = torch.empty(total, dtype=torch.uint8, device="cuda")
     ctx = orand.default_context().handle
     values = int(recs["length"].sum())
@@ -662,8 +699,8 @@ def main():
 
     frows, _keep = fill_rows(torch, orand, W, rank)
     head = frows[0]  # fill/philox4x32_10/u32: the headline kernel
-    wrows, _wkeep = walk_rows(torch, orand, W, rank)
-    rrows, _rkeep = ragged_rows(torch, orand, W, rank)
+    wrows, _wkeep = walk_rows(torch, orand, W, rank, world)
+    rrows, _rkeep = ragged_rows(torch, orand, W, rank, world)
     srows, _skeep = stream_test_rows(torch, orand, W, rank)
     # Step order: walks, ragged batch, stream tests, then the fills with the
     # headline Philox u32 fill last, right after the Philox f32 fill, so that
@@ -765,6 +802,31 @@ def main():
         "traffic": traffic, "share_of_step": row_table[head.name]["share_of_step"],
         "kernel": "fill_tile_kernel<philox4x32_10, u32, R=4, whole rows> (swizzled tile, TMA tensor store)",
         "peak_kind": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)"}
+    # Every fill of the 2^24 x 16 workload against both of its bounds: the
+    # measured copy bandwidth (bytes written) and the issue peak (its ncu
+    # warp-instruction count per launch over the event-timed duration), with
+    # the busiest pipe from the same capture.  The larger fraction names the
+    # bound.
+    issue = fill_issue_counts(source_hash(HEAD_KERNEL_SOURCES))
+    for r in rows:
+        if not hasattr(r, "gen"):
+            continue
+        t_s = statistics.mean(r.times_ms) * 1e-3
+        gbs = r.bytes_written / t_s / 1e9
+        e = {"kernel": "fill_tile_kernel<%s,%s>" % (W.GEN_NAMES[r.gen], W.DTYPE_NAMES[r.dtype]),
+             "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak},
+             "share_of_step": row_table[r.name]["share_of_step"]}
+        if (r.gen, r.dtype) in issue:
+            inst, pipe, pct = issue[(r.gen, r.dtype)]
+            e["issue"] = {"achieved": inst / t_s, "peak": ISSUE_PEAK_WARP_INST, "unit": "warp-instructions/s",
+                          "frac": inst / t_s / ISSUE_PEAK_WARP_INST, "warp_instructions_per_launch": inst,
+                          "busiest_pipe": pipe, "busiest_pipe_pct_of_peak": pct,
+                          "peak_kind": "derived: 148 SMs x 4 schedulers x 2.032 GHz"}
+            e["bound"] = "hbm" if e["hbm"]["frac"] >= e["issue"]["frac"] else "issue"
+        else:
+            e["issue"] = None
+            e["bound"] = "hbm"
+        rooflines["fill/%s/%s" % (W.GEN_NAMES[r.gen], W.DTYPE_NAMES[r.dtype])] = e
     # `roofline`: the dominant kernel of the step, the 2D walk (issue-bound),
     # with the DRAM bytes of one launch from ncu (the 2^24 positions; the
     # steps move no memory).

@@ -408,26 +408,42 @@ __device__ __forceinline__ float bm_radius(uint32_t w0)
 /* (cos, sin)(2 pi u2), u2 = (w1 >> 8) * 2^-24: quadrant q = round(4 u2),
  * r = 2 u2 - q/2 in [-1/4, 1/4] exactly, then a signed swap by q mod 4.
  * With a = w1 + 2^29 (mod 2^32; adding half a quadrant at bit 29 leaves the
- * low 8 bits alone), q mod 4 is a's top two bits and (4 u2 - q) 2^22 is its
- * bits 8..29 minus 2^21. */
-__device__ __forceinline__ void bm_cos_sin(uint32_t w1, float *c, float *s)
+ * low 8 bits alone), q mod 4 is a's top two bits and r = (bits 8..29 of a)
+ * 2^-23 - 1/4: one masked conversion (22 significant bits, exact) and one
+ * FMA whose exact result is representable.  Sine is negated for q = 2, 3
+ * (a's bit 31), cosine for q = 1, 2: bit 31 of a + 2^30, which is a's bit 31
+ * xor its bit 30. */
+__device__ __forceinline__ float bm_angle_r(uint32_t a)
 {
-    const uint32_t a = w1 + (1u << 29);
-    const float r = (float)((int)((a >> 8) & 0x3FFFFFu) - (1 << 21)) * 0x1p-23f; /* exact */
+    return fmaf(__uint2float_rn(a & 0x3FFFFF00u), 0x1p-31f, -0.25f);
+}
+__device__ __forceinline__ void bm_cos_sin_poly(float r, float *sn, float *cs)
+{
     const float t = r * r;
     float qs = fmaf(bm::QS3, t, bm::QS2);
     qs = fmaf(qs, t, bm::QS1);
     qs = fmaf(qs, t, bm::QS0);
-    const float sn = fmaf(r, bm::PI_HI, r * fmaf(t, qs, bm::PI_LO));
+    *sn = fmaf(r, bm::PI_HI, r * fmaf(t, qs, bm::PI_LO));
     float qc = fmaf(bm::QC4, t, bm::QC3);
     qc = fmaf(qc, t, bm::QC2);
     qc = fmaf(qc, t, bm::QC1);
     qc = fmaf(qc, t, bm::QC0);
-    const float cs = fmaf(t, qc, 1.0f);
+    *cs = fmaf(t, qc, 1.0f);
+}
+/* The quadrant's swap and signs applied to (sin, cos)(pi r) for the word w1. */
+__device__ __forceinline__ void bm_quadrant(uint32_t w1, float sn, float cs, float *c, float *s)
+{
+    const uint32_t a = w1 + (1u << 29), b = w1 + (3u << 29);
     const bool swap = (a >> 30) & 1u;
     const uint32_t vs = __float_as_uint(swap ? cs : sn), vc = __float_as_uint(swap ? sn : cs);
-    *s = __uint_as_float(vs ^ (a & 0x80000000u));              /* negate sin for q = 2, 3 */
-    *c = __uint_as_float(vc ^ ((a ^ (a << 1)) & 0x80000000u)); /* negate cos for q = 1, 2 */
+    *s = __uint_as_float(vs ^ (a & 0x80000000u));
+    *c = __uint_as_float(vc ^ (b & 0x80000000u));
+}
+__device__ __forceinline__ void bm_cos_sin(uint32_t w1, float *c, float *s)
+{
+    float sn, cs;
+    bm_cos_sin_poly(bm_angle_r(w1 + (1u << 29)), &sn, &cs);
+    bm_quadrant(w1, sn, cs, c, s);
 }
 
 /* Box-Muller pair (r cos 2 pi u2, r sin 2 pi u2) from two words. */
@@ -437,6 +453,100 @@ __device__ __forceinline__ float2 box_muller_f32(uint32_t w0, uint32_t w1)
     float c, s;
     bm_cos_sin(w1, &c, &s);
     return make_float2(r * c, r * s);
+}
+
+/* -------------------------------------------------- packed FP32 pairs
+ * Blackwell executes FP32 add, multiply and FMA on register pairs
+ * (add/mul/fma.rn.f32x2): one instruction, two lanes, each rounded exactly
+ * as the scalar operation would be.  The helpers below keep a pair in one
+ * 64-bit value (low half lane 0). */
+namespace x2 {
+__device__ __forceinline__ unsigned long long pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 unpack(unsigned long long v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long splat(float c) { return pack(c, c); }
+__device__ __forceinline__ unsigned long long fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+}  // namespace x2
+
+/* Both Box-Muller pairs of a group of four words, (w.x, w.y) and (w.z, w.w),
+ * as (z0, z1, z2, z3) bit patterns: the operations of bm_radius and
+ * bm_cos_sin done on packed pairs (lane 0 the first pair, lane 1 the
+ * second), so the same bits as two box_muller_f32 calls in about two thirds
+ * of the instructions.  The radius's tail is rearranged without changing a
+ * rounding: 2 ln u1 is -x exactly, so x - (x y)^2 is the negation of
+ * fma(x y, x y, 2 ln u1), folded into -0.5 y. */
+__device__ __forceinline__ uint4 box_muller2_f32(uint4 w)
+{
+    using namespace x2;
+    const uint32_t b0 = __float_as_uint(__uint2float_rn((w.x >> 8) + 1u));
+    const uint32_t b1 = __float_as_uint(__uint2float_rn((w.z >> 8) + 1u));
+    const uint32_t t0 = b0 - 0x4B3504F3u, t1 = b1 - 0x4B3504F3u;          /* see bm_radius */
+    const unsigned long long E = pack((float)((int)t0 >> 23), (float)((int)t1 >> 23));
+    const unsigned long long g = add(pack(__uint_as_float((t0 & 0x007FFFFFu) + 0x3F3504F3u),
+                                          __uint_as_float((t1 & 0x007FFFFFu) + 0x3F3504F3u)),
+                                     splat(-1.0f));
+    unsigned long long p = fma(splat(bm::PL8), g, splat(bm::PL7));
+    p = fma(p, g, splat(bm::PL6));
+    p = fma(p, g, splat(bm::PL5));
+    p = fma(p, g, splat(bm::PL4));
+    p = fma(p, g, splat(bm::PL3));
+    p = fma(p, g, splat(bm::PL2));
+    p = fma(p, g, splat(bm::PL1));
+    p = fma(p, g, splat(bm::PL0));
+    const unsigned long long lnf = fma(mul(g, g), p, g);
+    const unsigned long long lnu = fma(E, splat(bm::LN2_HI), fma(E, splat(bm::LN2_LO), lnf));
+    const unsigned long long x = fma(splat(-2.0f), lnu, splat(0.0f));      /* -2 ln u1 >= +0 */
+    const unsigned long long nx = mul(splat(2.0f), lnu);                    /* -x where x > 0 */
+    const float2 xs = unpack(x);
+    const unsigned long long y = pack(rsqrtf(xs.x), rsqrtf(xs.y));
+    const unsigned long long sx = mul(x, y);
+    const float2 rr = unpack(fma(mul(splat(-0.5f), y), fma(sx, sx, nx), sx));
+    const float ra = xs.x > 0.0f ? rr.x : 0.0f, rb = xs.y > 0.0f ? rr.y : 0.0f;
+    const unsigned long long r = fma(pack(__uint2float_rn((w.y + (1u << 29)) & 0x3FFFFF00u),
+                                          __uint2float_rn((w.w + (1u << 29)) & 0x3FFFFF00u)),
+                                     splat(0x1p-31f), splat(-0.25f));
+    const unsigned long long t = mul(r, r);
+    unsigned long long qs = fma(splat(bm::QS3), t, splat(bm::QS2));
+    qs = fma(qs, t, splat(bm::QS1));
+    qs = fma(qs, t, splat(bm::QS0));
+    const float2 sn = unpack(fma(r, splat(bm::PI_HI), mul(r, fma(t, qs, splat(bm::PI_LO)))));
+    unsigned long long qc = fma(splat(bm::QC4), t, splat(bm::QC3));
+    qc = fma(qc, t, splat(bm::QC2));
+    qc = fma(qc, t, splat(bm::QC1));
+    qc = fma(qc, t, splat(bm::QC0));
+    const float2 cs = unpack(fma(t, qc, splat(1.0f)));
+    float c0, s0, c1, s1;
+    bm_quadrant(w.y, sn.x, cs.x, &c0, &s0);
+    bm_quadrant(w.w, sn.y, cs.y, &c1, &s1);
+    const float2 z01 = unpack(mul(splat(ra), pack(c0, s0)));
+    const float2 z23 = unpack(mul(splat(rb), pack(c1, s1)));
+    return make_uint4(__float_as_uint(z01.x), __float_as_uint(z01.y), __float_as_uint(z23.x), __float_as_uint(z23.y));
 }
 
 /* Cosine half of a Box-Muller pair: r cos(2 pi u2), the first normal. */
@@ -501,16 +611,22 @@ __device__ __forceinline__ float bm_radius_walk(uint32_t w0)
  * the pair, with cos(theta + pi/2) = -sin(theta), and bit 31 (q >= 2)
  * negates both; theta's 22 bits stay in place, w1 & 0x3FFFFF00, with the
  * 2^-8 folded into the exact scale. */
-__device__ __forceinline__ void bm_cos_sin_walk(uint32_t w1, float *c, float *s)
+/* The quadrant's swap and signs for the walks' map, applied to the
+ * estimates sn, cs at theta. */
+__device__ __forceinline__ void bm_quadrant_walk(uint32_t w1, float sn, float cs, float *c, float *s)
 {
-    const float th = (float)(w1 & 0x3FFFFF00u) * (0x1p-31f * 3.14159265358979324f);
-    const float sn = sfu_sin(th), cs = sfu_cos(th);
     const bool odd = (w1 >> 30) & 1u;
     const float a = odd ? cs : sn;
     const float b = odd ? -sn : cs;
     const uint32_t flip = w1 & 0x80000000u;
     *s = __uint_as_float(__float_as_uint(a) ^ flip);
     *c = __uint_as_float(__float_as_uint(b) ^ flip);
+}
+
+__device__ __forceinline__ void bm_cos_sin_walk(uint32_t w1, float *c, float *s)
+{
+    const float th = (float)(w1 & 0x3FFFFF00u) * (0x1p-31f * 3.14159265358979324f);
+    bm_quadrant_walk(w1, sfu_sin(th), sfu_cos(th), c, s);
 }
 
 __device__ __forceinline__ float2 box_muller_walk_f32(uint32_t w0, uint32_t w1)

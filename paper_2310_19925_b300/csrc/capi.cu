@@ -6,6 +6,8 @@
 #include <mutex>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "ctx.cuh"
 
@@ -28,6 +30,24 @@ void log_cuda_failure(const char *what, const char *file, int line, cudaError_t 
 {
     if (log_enabled()) fprintf(stderr, "orand: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
 }
+
+bool alloc_blocked()
+{
+    const char *v = getenv("ORAND_FAIL_ALLOC");
+    return v && v[0] == '1';
+}
+
+bool nvtx_enabled()
+{
+    static const bool on = [] {
+        const char *v = getenv("ORAND_NVTX");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+
+void nvtx_push(const char *name) { nvtxRangePushA(name); }
+void nvtx_pop() { nvtxRangePop(); }
 
 namespace {
 constexpr int kMaxDevices = 64;
@@ -94,6 +114,7 @@ orand_status_t ctx_scratch(orand_ctx_t ctx, size_t bytes, void **ptr)
             ctx->scratch_bytes = 0;
         }
         void *p = nullptr;
+        if (alloc_blocked()) return ORAND_ERR_ALLOC;
         if (cudaMalloc(&p, want) != cudaSuccess) {
             set_last_cuda_error(cudaGetLastError());
             return ORAND_ERR_ALLOC;
@@ -115,11 +136,16 @@ orand_status_t orand_ctx_create(orand_ctx_t *ctx)
 {
     if (ctx == nullptr) return ORAND_ERR_INVALID_ARG;
     *ctx = nullptr;
+    // The host object first, so an allocation failure is reported as such
+    // whatever the device's state.
+    orand_ctx_s *c = orand_impl::alloc_blocked() ? nullptr : new (std::nothrow) orand_ctx_s();
+    if (c == nullptr) return ORAND_ERR_ALLOC;
     orand_impl::DeviceInfo info;
     orand_status_t st = orand_impl::current_device(&info);
-    if (st != ORAND_OK) return st;
-    orand_ctx_s *c = new (std::nothrow) orand_ctx_s();
-    if (c == nullptr) return ORAND_ERR_ALLOC;
+    if (st != ORAND_OK) {
+        delete c;
+        return st;
+    }
     c->device = info.device;
     *ctx = c;
     return ORAND_OK;
@@ -146,7 +172,7 @@ const char *orand_status_string(orand_status_t status)
     case ORAND_ERR_INVALID_ARG: return "ORAND_ERR_INVALID_ARG: null pointer, unknown enum or bad field";
     case ORAND_ERR_OVERFLOW: return "ORAND_ERR_OVERFLOW: size overflows, or a stream needs more than 2^32 words";
     case ORAND_ERR_ALIGNMENT: return "ORAND_ERR_ALIGNMENT: pointer or offset not aligned to its element size";
-    case ORAND_ERR_ALLOC: return "ORAND_ERR_ALLOC: context allocation failed";
+    case ORAND_ERR_ALLOC: return "ORAND_ERR_ALLOC: a library allocation (context, scratch, batch tables) failed";
     case ORAND_ERR_CUDA: return "ORAND_ERR_CUDA: CUDA runtime call or launch failed";
     case ORAND_ERR_DEVICE_TIMEOUT: return "ORAND_ERR_DEVICE_TIMEOUT: a device-side wait gave up";
     case ORAND_ERR_UNSUPPORTED: return "ORAND_ERR_UNSUPPORTED: device is not compute capability 10.3 (sm_103a)";

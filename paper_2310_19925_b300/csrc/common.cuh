@@ -38,6 +38,34 @@ void log_cuda_failure(const char *what, const char *file, int line, cudaError_t 
         }                                                                               \
     } while (0)
 
+// Allocation-failure injection for tests: while ORAND_FAIL_ALLOC=1 is set
+// in the environment, every allocation the library would make (contexts,
+// context scratch, the ragged batcher's state, tables and pinned staging)
+// is refused before the allocator is called, and the call returns
+// ORAND_ERR_ALLOC.  Read at each allocation (they are rare), so a test can
+// switch it on and off inside one process.
+bool alloc_blocked();
+
+// NVTX ranges named after the C-ABI call, around each call that launches
+// work, for profilers; off unless ORAND_NVTX=1 at the first call.
+bool nvtx_enabled();
+void nvtx_push(const char *name);
+void nvtx_pop();
+struct NvtxRange {
+    bool on;
+    explicit NvtxRange(const char *name) : on(nvtx_enabled())
+    {
+        if (on) nvtx_push(name);
+    }
+    ~NvtxRange()
+    {
+        if (on) nvtx_pop();
+    }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define ORAND_NVTX_RANGE(name) ::orand_impl::NvtxRange orand_nvtx_range_(name)
+
 struct DeviceInfo {
     int device;
     int sm_count;

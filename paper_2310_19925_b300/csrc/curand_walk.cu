@@ -117,6 +117,7 @@ size_t orand_walk2d_curand_state_bytes(void) { return sizeof(curandStatePhilox4_
 orand_status_t orand_walk2d_curand_setup(const orand_walk2d_t *p, void *states, float *pos_out, uint64_t curand_seed,
                                          cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk2d_curand_setup");
     unsigned grid;
     float s;
     orand_status_t st = walk2d_curand_args(p, pos_out, &grid, &s);
@@ -132,6 +133,7 @@ orand_status_t orand_walk2d_curand_setup(const orand_walk2d_t *p, void *states, 
 
 orand_status_t orand_walk2d_curand_run(const orand_walk2d_t *p, void *states, float *pos, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk2d_curand_run");
     unsigned grid;
     float s;
     orand_status_t st = walk2d_curand_args(p, pos, &grid, &s);
@@ -150,6 +152,7 @@ orand_status_t orand_walk2d_curand_run(const orand_walk2d_t *p, void *states, fl
 orand_status_t orand_walk2d_curand_fused(const orand_walk2d_t *p, float *pos_out, uint64_t curand_seed,
                                          cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk2d_curand_fused");
     unsigned grid;
     float s;
     orand_status_t st = walk2d_curand_args(p, pos_out, &grid, &s);

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256) engine_draws_kernel(uint64_t seed, uint32
 extern "C" orand_status_t orand_engine_draws(orand_gen_t gen, uint64_t seed, uint32_t counter, uint32_t first_word,
                                              uint64_t n_threads, uint32_t n_rounds, void *out, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_engine_draws");
     using namespace orand_impl;
     if ((unsigned)gen > ORAND_TYCHE) return ORAND_ERR_INVALID_ARG;
     if (gen == ORAND_TYCHE && first_word != 0) return ORAND_ERR_INVALID_ARG;

@@ -572,6 +572,7 @@ extern "C" {
 orand_status_t orand_map_words(orand_dtype_t dtype, const uint32_t *words, uint64_t n_values, void *out,
                                cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_map_words");
     return orand_impl::map_words_launch((int)dtype, words, n_values, out, stream);
 }
 
@@ -579,6 +580,7 @@ orand_status_t orand_map_words(orand_dtype_t dtype, const uint32_t *words, uint6
 orand_status_t orand_fill(orand_gen_t gen, orand_dtype_t dtype, uint64_t seed, uint32_t counter,
                           uint64_t n_streams, uint64_t draws_per_stream, void *out, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill");
     return orand_impl::fill_launch((int)gen, (int)dtype, seed, counter, 0, n_streams, draws_per_stream, out,
                                    stream);
 }
@@ -587,6 +589,7 @@ orand_status_t orand_fill_streams(orand_gen_t gen, orand_dtype_t dtype, uint64_t
                                   uint64_t first_stream, uint64_t n_streams, uint64_t draws_per_stream, void *out,
                                   cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill_streams");
     return orand_impl::fill_launch((int)gen, (int)dtype, seed, counter, first_stream, n_streams, draws_per_stream,
                                    out, stream);
 }
@@ -594,12 +597,14 @@ orand_status_t orand_fill_streams(orand_gen_t gen, orand_dtype_t dtype, uint64_t
 orand_status_t orand_fill_u32(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                               uint64_t draws_per_stream, uint32_t *out, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill_u32");
     return orand_impl::fill_launch((int)gen, ORAND_U32, seed, counter, 0, n_streams, draws_per_stream, out, stream);
 }
 
 orand_status_t orand_fill_uniform_f32(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                                       uint64_t draws_per_stream, float *out, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill_uniform_f32");
     return orand_impl::fill_launch((int)gen, ORAND_F32_UNIFORM, seed, counter, 0, n_streams, draws_per_stream,
                                    out, stream);
 }
@@ -607,6 +612,7 @@ orand_status_t orand_fill_uniform_f32(orand_gen_t gen, uint64_t seed, uint32_t c
 orand_status_t orand_fill_uniform_f64(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                                       uint64_t draws_per_stream, double *out, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill_uniform_f64");
     return orand_impl::fill_launch((int)gen, ORAND_F64_UNIFORM, seed, counter, 0, n_streams, draws_per_stream,
                                    out, stream);
 }
@@ -614,6 +620,7 @@ orand_status_t orand_fill_uniform_f64(orand_gen_t gen, uint64_t seed, uint32_t c
 orand_status_t orand_fill_normal_f32(orand_gen_t gen, uint64_t seed, uint32_t counter, uint64_t n_streams,
                                      uint64_t draws_per_stream, float *out, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill_normal_f32");
     return orand_impl::fill_launch((int)gen, ORAND_F32_NORMAL, seed, counter, 0, n_streams, draws_per_stream,
                                    out, stream);
 }

@@ -203,6 +203,7 @@ extern "C" {
 
 orand_status_t orand_langevin2d_init(const orand_langevin2d_t *p, orand_particle_t *particles, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_langevin2d_init");
     LangevinArgs a;
     orand_status_t st = langevin_args(p, &a);
     if (st != ORAND_OK || a.n == 0) return st;
@@ -216,6 +217,7 @@ orand_status_t orand_langevin2d_init(const orand_langevin2d_t *p, orand_particle
 orand_status_t orand_langevin2d_step(const orand_langevin2d_t *p, orand_particle_t *particles, uint32_t counter,
                                      cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_langevin2d_step");
     LangevinArgs a;
     orand_status_t st = langevin_args(p, &a);
     if (st != ORAND_OK || a.n == 0) return st;
@@ -229,6 +231,7 @@ orand_status_t orand_langevin2d_step(const orand_langevin2d_t *p, orand_particle
 orand_status_t orand_langevin2d_fused(const orand_langevin2d_t *p, orand_particle_t *particles,
                                       uint32_t first_counter, uint32_t steps, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_langevin2d_fused");
     LangevinArgs a;
     orand_status_t st = langevin_args(p, &a);
     if (st != ORAND_OK || a.n == 0) return st;
@@ -243,6 +246,7 @@ orand_status_t orand_langevin2d_fused(const orand_langevin2d_t *p, orand_particl
 orand_status_t orand_langevin2d_run_per_step(const orand_langevin2d_t *p, orand_particle_t *particles,
                                              uint32_t first_counter, uint32_t steps, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_langevin2d_run_per_step");
     LangevinArgs a;
     orand_status_t st = langevin_args(p, &a);
     if (st != ORAND_OK || a.n == 0) return st;
@@ -261,6 +265,7 @@ size_t orand_langevin2d_curand_state_bytes(void) { return sizeof(curandStatePhil
 orand_status_t orand_langevin2d_curand_setup(const orand_langevin2d_t *p, orand_particle_t *particles, void *states,
                                              uint64_t curand_seed, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_langevin2d_curand_setup");
     LangevinArgs a;
     orand_status_t st = langevin_args(p, &a);
     if (st != ORAND_OK || a.n == 0) return st;
@@ -278,6 +283,7 @@ orand_status_t orand_langevin2d_curand_setup(const orand_langevin2d_t *p, orand_
 orand_status_t orand_langevin2d_curand_step(const orand_langevin2d_t *p, orand_particle_t *particles, void *states,
                                             cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_langevin2d_curand_step");
     LangevinArgs a;
     orand_status_t st = langevin_args(p, &a);
     if (st != ORAND_OK || a.n == 0) return st;
@@ -296,6 +302,7 @@ orand_status_t orand_langevin2d_curand_step(const orand_langevin2d_t *p, orand_p
 extern "C" orand_status_t orand_langevin2d_curand_run(const orand_langevin2d_t *p, orand_particle_t *particles,
                                                       void *states, uint32_t steps, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_langevin2d_curand_run");
     LangevinArgs a;
     orand_status_t st = langevin_args(p, &a);
     if (st != ORAND_OK || a.n == 0) return st;

@@ -21,15 +21,20 @@
 // Autotuning: block size, chunk size and store width (16/8/4-byte stores)
 // are timed on the caller's batch the first time a size class is seen.  The
 // output is written again each time with the same bits.  The fastest
-// configuration is kept per size class in the context.
+// configuration is kept per size class in the context and, keyed by the GPU's
+// name as well, in a small file that later processes read instead of tuning.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <tuple>
 #include <vector>
+
+#include <sys/stat.h>
 
 #include "common.cuh"
 #include "ctx.cuh"
@@ -202,8 +207,12 @@ __device__ __forceinline__ void chunk_dt(const RaggedReq &q, char *out, uint64_t
     }
 }
 
+// Block sizes up to 1024 threads are accepted (orand_ragged_set_config), so
+// the kernels are compiled to fit 1024-thread blocks (at most 64 registers).
+constexpr int kRaggedMaxBlock = 1024;
+
 template <int SW>
-__global__ void ragged_kernel(char *table)
+__global__ void __launch_bounds__(kRaggedMaxBlock) ragged_kernel(char *table)
 {
     const RaggedHeader h = *reinterpret_cast<const RaggedHeader *>(table);
     const RaggedReq *reqs = reinterpret_cast<const RaggedReq *>(table + h.off_reqs);
@@ -292,7 +301,7 @@ __device__ __forceinline__ void convert_groups(char *base, uint64_t g0, uint64_t
     }
 }
 
-__global__ void ragged_convert_kernel(char *table)
+__global__ void __launch_bounds__(kRaggedMaxBlock) ragged_convert_kernel(char *table)
 {
     const RaggedHeader h = *reinterpret_cast<const RaggedHeader *>(table);
     const RaggedReq *reqs = reinterpret_cast<const RaggedReq *>(table + h.off_reqs);
@@ -358,7 +367,7 @@ struct RaggedState {
 
 static RaggedState *state_of(orand_ctx_t ctx)
 {
-    if (!ctx->ragged) ctx->ragged = new (std::nothrow) RaggedState();
+    if (!ctx->ragged && !alloc_blocked()) ctx->ragged = new (std::nothrow) RaggedState();
     return (RaggedState *)ctx->ragged;
 }
 
@@ -552,6 +561,7 @@ static orand_status_t ensure_buffers(RaggedState *s, size_t bytes)
             s->d_bytes = 0;
         }
         const size_t want = align_up(bytes + bytes / 4, (size_t)1 << 20);
+        if (alloc_blocked()) return ORAND_ERR_ALLOC;
         if (cudaMalloc(&s->d_tables, want) != cudaSuccess) {
             set_last_cuda_error(cudaGetLastError());
             return ORAND_ERR_ALLOC;
@@ -567,6 +577,7 @@ static orand_status_t ensure_buffers(RaggedState *s, size_t bytes)
             s->h_bytes = 0;
         }
         const size_t want = align_up(bytes + bytes / 4, (size_t)1 << 20);
+        if (alloc_blocked()) return ORAND_ERR_ALLOC;
         if (cudaHostAlloc(&s->h_staging, want, cudaHostAllocDefault) != cudaSuccess) {
             set_last_cuda_error(cudaGetLastError());
             return ORAND_ERR_ALLOC;
@@ -675,6 +686,114 @@ static bool env_flag(const char *name, bool dflt)
     return !(v[0] == '0' || v[0] == 'n' || v[0] == 'N' || v[0] == 'f' || v[0] == 'F');
 }
 
+// ----------------------------------------------- persistent tuning table
+//
+// Tuned configurations outlive the process in a small text file, one line
+// per (GPU name, size class): "<gpu> <log2 values> <log2 requests> <tyche>
+// <block> <chunk_values> <store_bytes> <ctas_per_sm>", GPU names with
+// spaces written as '_'.  The file is ORAND_TUNE_CACHE (empty, "0" or "off":
+// no file), else $XDG_CACHE_HOME/orand/ragged_tune.txt, else
+// $HOME/.cache/orand/ragged_tune.txt.  It is read once per process and
+// appended to after each new tuning; unreadable or malformed lines are
+// skipped, so a bad file costs a re-tune, never a wrong result (every
+// configuration writes the same bits).
+using TuneKey = std::tuple<std::string, int, int, int>;
+
+struct TuneFile {
+    std::mutex mu;
+    bool loaded = false;
+    std::string path;
+    std::map<TuneKey, RaggedConfig> table;
+};
+
+static TuneFile &tune_file()
+{
+    static TuneFile f;
+    return f;
+}
+
+static std::string tune_cache_path()
+{
+    const char *v = getenv("ORAND_TUNE_CACHE");
+    if (v) {
+        if (!*v || !strcmp(v, "0") || !strcmp(v, "off")) return std::string();
+        return v;
+    }
+    const char *x = getenv("XDG_CACHE_HOME");
+    if (x && *x) return std::string(x) + "/orand/ragged_tune.txt";
+    const char *h = getenv("HOME");
+    if (h && *h) return std::string(h) + "/.cache/orand/ragged_tune.txt";
+    return std::string();
+}
+
+static std::string gpu_name(int device)
+{
+    static std::mutex mu;
+    static std::map<int, std::string> names;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = names.find(device);
+    if (it != names.end()) return it->second;
+    cudaDeviceProp prop;
+    std::string n = cudaGetDeviceProperties(&prop, device) == cudaSuccess ? prop.name : "unknown";
+    for (char &c : n)
+        if (c == ' ' || c == '\t' || c == '\n') c = '_';
+    names[device] = n;
+    return n;
+}
+
+// Caller holds f.mu.
+static void tune_file_load(TuneFile &f)
+{
+    if (f.loaded) return;
+    f.loaded = true;
+    f.path = tune_cache_path();
+    if (f.path.empty()) return;
+    FILE *fp = fopen(f.path.c_str(), "r");
+    if (!fp) return;
+    char name[256];
+    int lv, ln, ty;
+    unsigned bl, ch, sw, cps;
+    char line[512];
+    while (fgets(line, sizeof line, fp)) {
+        if (sscanf(line, "%255s %d %d %d %u %u %u %u", name, &lv, &ln, &ty, &bl, &ch, &sw, &cps) != 8) continue;
+        RaggedConfig c;
+        c.block = bl;
+        c.chunk_values = ch;
+        c.store_bytes = sw;
+        c.ctas_per_sm = cps;
+        if (valid_config(c)) f.table[TuneKey(name, lv, ln, ty)] = c;
+    }
+    fclose(fp);
+}
+
+static bool tune_file_lookup(const TuneKey &k, RaggedConfig *cfg)
+{
+    TuneFile &f = tune_file();
+    std::lock_guard<std::mutex> lock(f.mu);
+    tune_file_load(f);
+    auto it = f.table.find(k);
+    if (it == f.table.end()) return false;
+    *cfg = it->second;
+    return true;
+}
+
+static void tune_file_store(const TuneKey &k, const RaggedConfig &c)
+{
+    TuneFile &f = tune_file();
+    std::lock_guard<std::mutex> lock(f.mu);
+    tune_file_load(f);
+    f.table[k] = c;
+    if (f.path.empty()) return;
+    // Create the parent directories if needed (best effort; existing ones stay).
+    for (size_t i = f.path.find('/', 1); i != std::string::npos; i = f.path.find('/', i + 1))
+        mkdir(f.path.substr(0, i).c_str(), 0755);
+    FILE *fp = fopen(f.path.c_str(), "a");
+    if (!fp) return;
+    fprintf(fp, "%s %d %d %d %u %u %u %u\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+            c.block, c.chunk_values, c.store_bytes, c.ctas_per_sm);
+    fclose(fp);
+}
+
 orand_status_t ragged_serve(orand_ctx_t ctx, const orand_request_t *reqs, size_t n, void *out_base,
                             uint64_t out_bytes, cudaStream_t stream)
 {
@@ -701,8 +820,12 @@ orand_status_t ragged_serve(orand_ctx_t ctx, const orand_request_t *reqs, size_t
     } else if (s->tuned.count(klass)) {
         cfg = s->tuned[klass];
     } else if (env_flag("ORAND_AUTOTUNE", true)) {
-        if (s->batch_pending) cudaStreamWaitEvent(stream, s->batch_done, 0);
-        if ((st = autotune(s, reqs, n, out, out_bytes, stream, &cfg)) != ORAND_OK) return st;
+        const TuneKey key(gpu_name(ctx->device), std::get<0>(klass), std::get<1>(klass), std::get<2>(klass));
+        if (!tune_file_lookup(key, &cfg)) {
+            if (s->batch_pending) cudaStreamWaitEvent(stream, s->batch_done, 0);
+            if ((st = autotune(s, reqs, n, out, out_bytes, stream, &cfg)) != ORAND_OK) return st;
+            tune_file_store(key, cfg);
+        }
         s->tuned[klass] = cfg;
     }
     if (cfg.chunk_values != plan.chunk_values &&
@@ -775,12 +898,14 @@ extern "C" {
 orand_status_t orand_fill_ragged(orand_ctx_t ctx, const orand_request_t *reqs, size_t n, void *out_base,
                                  uint64_t out_bytes, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill_ragged");
     return ragged_serve(ctx, reqs, n, out_base, out_bytes, stream);
 }
 
 orand_status_t orand_fill_ragged_serial(const orand_request_t *reqs, size_t n, void *out_base, uint64_t out_bytes,
                                         cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill_ragged_serial");
     if (n == 0) return ORAND_OK;
     if (reqs == nullptr) return ORAND_ERR_INVALID_ARG;
     Plan plan;

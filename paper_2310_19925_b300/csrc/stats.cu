@@ -626,6 +626,7 @@ orand_status_t orand_fill_micro_streams(orand_gen_t gen, uint64_t seed, uint64_t
                                         uint32_t counter_first, uint32_t n_counters, uint32_t *out,
                                         cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_fill_micro_streams");
     if ((unsigned)gen > ORAND_TYCHE || draws == 0 || draws > 64) return ORAND_ERR_INVALID_ARG;
     if (n_counters > 0 && (uint64_t)counter_first + n_counters - 1 > UINT32_MAX) return ORAND_ERR_OVERFLOW;
     uint64_t n_micro, n_words;
@@ -660,6 +661,7 @@ orand_status_t orand_fill_micro_streams(orand_gen_t gen, uint64_t seed, uint64_t
 orand_status_t orand_stat_tuples(const uint32_t *words, uint64_t n_words, uint32_t t, uint32_t bits,
                                  uint32_t shift, uint32_t stride, uint64_t *counts, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_stat_tuples");
     if (t < 1 || t > 4 || bits < 1 || t * bits > 14 || shift + bits > 32 || stride < 1) return ORAND_ERR_INVALID_ARG;
     orand_status_t st = check_buf(counts, 8);
     if (st != ORAND_OK) return st;
@@ -697,6 +699,7 @@ orand_status_t orand_stat_tuples(const uint32_t *words, uint64_t n_words, uint32
 orand_status_t orand_stat_gaps(orand_ctx_t ctx, const uint32_t *words, uint64_t n_words, uint64_t lo, uint64_t hi,
                                uint32_t t_max, uint64_t *counts, uint64_t *carry, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_stat_gaps");
     if (lo >= hi || hi > (1ull << 32) || t_max < 1 || t_max > 4096) return ORAND_ERR_INVALID_ARG;
     orand_status_t st;
     if ((st = check_buf(counts, 8)) != ORAND_OK || (st = check_buf(carry, 8)) != ORAND_OK) return st;
@@ -728,6 +731,7 @@ orand_status_t orand_stat_gaps(orand_ctx_t ctx, const uint32_t *words, uint64_t 
 orand_status_t orand_stat_birthday(const uint32_t *words, uint64_t n_words, uint32_t log2_n, uint32_t bits,
                                    uint32_t shift, uint32_t r_max, uint64_t *counts, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_stat_birthday");
     if (log2_n < 2 || log2_n > 12 || bits < 1 || bits > 32 || shift + bits > 32 || r_max < 1 || r_max > 4096)
         return ORAND_ERR_INVALID_ARG;
     orand_status_t st = check_buf(counts, 8);

@@ -27,16 +27,21 @@ struct Vals {
 };
 
 // The group's values as a 16-byte bit pattern, in memory order: 4 x u32,
-// 4 x f32 (uniform, or normals z0 z1 of pair (w.x, w.y) then of (w.z, w.w)),
+// 4 x f32 (uniform, or normals z0 z1 of pair (w.x, w.y) then of (w.z, w.w),
+// both pairs evaluated on packed FP32 pairs),
 // or 2 x f64 (from (w.x, w.y) and (w.z, w.w)).  BRANCH_FREE selects the
 // branch-free FP64 map (same bits) for latency-bound callers.
 template <int DT, bool BRANCH_FREE = false>
 __device__ __forceinline__ uint4 group_bits(uint4 w)
 {
     if (DT == ORAND_U32) return w;
-    if (DT == ORAND_F32_UNIFORM)
-        return make_uint4(__float_as_uint(orand::u01_f32(w.x)), __float_as_uint(orand::u01_f32(w.y)),
-                          __float_as_uint(orand::u01_f32(w.z)), __float_as_uint(orand::u01_f32(w.w)));
+    if (DT == ORAND_F32_UNIFORM) {
+        // u01_f32 on each word, the exact scaling by 2^-24 done on packed pairs.
+        using namespace orand::x2;
+        const float2 a = unpack(mul(pack(__uint2float_rn(w.x >> 8), __uint2float_rn(w.y >> 8)), splat(0x1p-24f)));
+        const float2 b = unpack(mul(pack(__uint2float_rn(w.z >> 8), __uint2float_rn(w.w >> 8)), splat(0x1p-24f)));
+        return make_uint4(__float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(b.x), __float_as_uint(b.y));
+    }
     if (DT == ORAND_F64_UNIFORM) {
         if (!BRANCH_FREE && __builtin_expect(min(w.x, w.z) >= (1u << 20), 1)) {
             // Both high words >= 2^20 (all but about 2^-11 of the groups):
@@ -50,9 +55,7 @@ __device__ __forceinline__ uint4 group_bits(uint4 w)
         const unsigned long long b = __double_as_longlong(db);
         return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
     }
-    const float2 p = orand::box_muller_f32(w.x, w.y);
-    const float2 q = orand::box_muller_f32(w.z, w.w);
-    return make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(q.x), __float_as_uint(q.y));
+    return orand::box_muller2_f32(w);
 }
 
 // Masked element stores of a group's bits: values j0 + i for i < V and

@@ -77,21 +77,67 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 
 // ------------------------------------------------------------------ 2D walk
 
-// The 2D kernel is bound by instruction issue (67 operations per
+// The 2D kernel is bound by instruction issue (67 scalar operations per
 // particle-step, nearly all of them the Philox rounds and Box-Muller).  One
 // particle per thread; the position sum is compensated per block of
 // kSumBlock steps (plain FMA sums inside a block, a Kahan add of each block
 // sum), which saves the per-step compensation while keeping the rounding
 // error of the whole walk at the level of one FP32 rounding per block sum.
-// A full block runs a constant-trip-count loop unrolled by 4, which gives
-// the schedulers four steps' independent Philox chains; with the launch
-// bound of one block per SM, ptxas keeps the round keys in registers.
-// Measured on B300 (full walk, 2^24 x 10^4): 433.9 ms, against 437.9 with
-// two particles per thread (unroll 2, 90 registers); three or four per
-// thread measured slower still, and so did launch bounds that fit 32 or 40
-// warps per SM (436.6-446.1 ms).
+// A full block takes its steps in pairs: the two steps' Philox blocks are
+// independent chains, and the FP32 parts of their Box-Muller maps and sums
+// run as packed pairs (one f32x2 instruction for both steps; each lane is
+// rounded as the scalar operation, so every normal has the same bits; only
+// the block sum is split into an even-step and an odd-step half).  The loop
+// over the 8 pairs is unrolled by 2, and with the launch bound of one block
+// per SM ptxas keeps the round keys in registers (66 registers).  Measured on
+// B300 (full walk, 2^24 x 10^4): 425.5 ms against 433.8 with scalar steps
+// unrolled by 4; pairs unrolled by 1 or 4 took 436.3 and 427.3 ms.  Earlier,
+// with scalar steps: two particles per thread 437.9 ms, three or four
+// slower still, and launch bounds that fit 32 or 40 warps per SM
+// 436.6-446.1 ms.
 constexpr int kWalk2dBlock = 256;
 constexpr uint32_t kSumBlock = 16;
+
+// The walks' Box-Muller map (bm_radius_walk, bm_cos_sin_walk) for two
+// pairs at once, (radius word, angle word) = (u_a, t_a) in lane 0 and
+// (u_b, t_b) in lane 1, with its FP32 arithmetic on packed pairs (each lane
+// rounded as the scalar map, so the same bits): the radii as a packed pair,
+// and each angle's quadrant-adjusted cosine and sine.
+__device__ __forceinline__ unsigned long long walk_map_x2(uint32_t u_a, uint32_t t_a, uint32_t u_b, uint32_t t_b,
+                                                          float &ca, float &sa, float &cb, float &sb)
+{
+    using namespace orand::x2;
+    const unsigned long long u1 = mul(pack(__uint2float_rn((u_a >> 8) + 1u), __uint2float_rn((u_b >> 8) + 1u)),
+                                      splat(0x1p-24f));
+    const unsigned long long v = fma(u1, splat(-1.0f), splat(1.0f));              /* 1 - u1 */
+    unsigned long long p2 = fma(v, splat(2.0f / 6.0f), splat(0.4f));
+    p2 = fma(p2, v, splat(0.5f));
+    p2 = fma(p2, v, splat(2.0f / 3.0f));
+    p2 = fma(p2, v, splat(1.0f));
+    p2 = fma(p2, v, splat(2.0f));
+    const float2 x_series = unpack(mul(v, p2));
+    const float2 uu = unpack(u1);
+    const float2 x_log = unpack(mul(splat(-1.3862943611198906f), pack(orand::sfu_lg2(uu.x), orand::sfu_lg2(uu.y))));
+    const float2 vv = unpack(v);
+    const float xa = vv.x < 0.0625f ? x_series.x : x_log.x, xb = vv.y < 0.0625f ? x_series.y : x_log.y;
+    const float2 th = unpack(mul(pack((float)(t_a & 0x3FFFFF00u), (float)(t_b & 0x3FFFFF00u)),
+                                 splat(0x1p-31f * 3.14159265358979324f)));
+    orand::bm_quadrant_walk(t_a, orand::sfu_sin(th.x), orand::sfu_cos(th.x), &ca, &sa);
+    orand::bm_quadrant_walk(t_b, orand::sfu_sin(th.y), orand::sfu_cos(th.y), &cb, &sb);
+    return pack(orand::sfu_sqrt(xa), orand::sfu_sqrt(xb));
+}
+
+// Steps t (lane 0) and t + 1 (lane 1) of a 2D walk from their Philox blocks
+// wa, wb, accumulated into the packed block sums.
+__device__ __forceinline__ void walk2d_step_pair(uint4 wa, uint4 wb, unsigned long long &sxx,
+                                                 unsigned long long &syy)
+{
+    using namespace orand::x2;
+    float ca, sa, cb, sb;
+    const unsigned long long r = walk_map_x2(wa.x, wa.y, wb.x, wb.y, ca, sa, cb, sb);
+    sxx = fma(r, pack(ca, cb), sxx);
+    syy = fma(r, pack(sa, sb), syy);
+}
 
 __global__ void __launch_bounds__(kWalk2dBlock, 1) walk2d_kernel(uint64_t n, uint64_t p_first, uint64_t seed,
                                                                 uint32_t steps, float s, float2 *__restrict__ out)
@@ -106,20 +152,24 @@ __global__ void __launch_bounds__(kWalk2dBlock, 1) walk2d_kernel(uint64_t n, uin
     for (uint32_t done = 0; done < steps;) {
         const uint32_t len = min(kSumBlock, steps - done);
         float sx = 0.f, sy = 0.f;
-        auto step = [&](uint32_t t) {
-            const uint4 w = keys.block(0u, t);
-            // (r cos, r sin); the block sum is scaled by s once, at the flush.
-            const float r = orand::bm_radius_walk(w.x);
-            float c, sn;
-            orand::bm_cos_sin_walk(w.y, &c, &sn);
-            sx = fmaf(r, c, sx);
-            sy = fmaf(r, sn, sy);
-        };
         if (len == kSumBlock) {
-#pragma unroll 4
-            for (uint32_t k = 1; k <= kSumBlock; ++k) step(done + k);
+            unsigned long long sxx = orand::x2::splat(0.0f), syy = orand::x2::splat(0.0f);
+#pragma unroll 2
+            for (uint32_t k = 1; k <= kSumBlock; k += 2)
+                walk2d_step_pair(keys.block(0u, done + k), keys.block(0u, done + k + 1), sxx, syy);
+            const float2 a = orand::x2::unpack(sxx), b = orand::x2::unpack(syy);
+            sx = a.x + a.y;
+            sy = b.x + b.y;
         } else {
-            for (uint32_t k = 1; k <= len; ++k) step(done + k);
+            for (uint32_t k = 1; k <= len; ++k) {
+                // (r cos, r sin); the block sum is scaled by s once, at the flush.
+                const uint4 w = keys.block(0u, done + k);
+                const float r = orand::bm_radius_walk(w.x);
+                float c, sn;
+                orand::bm_cos_sin_walk(w.y, &c, &sn);
+                sx = fmaf(r, c, sx);
+                sy = fmaf(r, sn, sy);
+            }
         }
         kahan_add(x, cx, s * sx);
         kahan_add(y, cy, s * sy);
@@ -146,13 +196,17 @@ struct Walk3dArgs {
     double decay_last;  // (1 - kappa dt)^(steps - (nseg - 1) K): the last, possibly short, segment
 };
 
+// z_t: the pair (w.x, w.y) gives z0 = r cos, z1 = r sin, the pair (w.z, w.w)
+// the cosine z2 = r' cos'; both pairs' maps run on packed FP32 pairs.
 __device__ __forceinline__ void walk3d_normals(const orand::PhiloxKeys &keys, uint32_t t_counter, float z[3])
 {
     const uint4 w = keys.block(0u, t_counter);
-    const float2 a = orand::box_muller_walk_f32(w.x, w.y);
-    z[0] = a.x;
-    z[1] = a.y;
-    z[2] = orand::box_muller_cos_walk_f32(w.z, w.w);
+    float ca, sa, cb, sb;
+    const unsigned long long r = walk_map_x2(w.x, w.y, w.z, w.w, ca, sa, cb, sb);
+    const float2 zz = orand::x2::unpack(orand::x2::mul(r, orand::x2::pack(ca, cb)));
+    z[0] = zz.x;
+    z[1] = orand::x2::unpack(r).x * sa;
+    z[2] = zz.y;
 }
 
 // sigma sqrt(dt) * (z0, z1, z2) with the scale folded into the two radii.
@@ -160,14 +214,13 @@ __device__ __forceinline__ void walk3d_scaled_normals(const orand::PhiloxKeys &k
                                                       float scale, float z[3])
 {
     const uint4 w = keys.block(0u, t_counter);
-    const float ra = scale * orand::bm_radius_walk(w.x);
-    const float rb = scale * orand::bm_radius_walk(w.z);
     float ca, sa, cb, sb;
-    orand::bm_cos_sin_walk(w.y, &ca, &sa);
-    orand::bm_cos_sin_walk(w.w, &cb, &sb);
-    z[0] = ra * ca;
-    z[1] = ra * sa;
-    z[2] = rb * cb;
+    const unsigned long long r =
+        orand::x2::mul(orand::x2::splat(scale), walk_map_x2(w.x, w.y, w.z, w.w, ca, sa, cb, sb));
+    const float2 zz = orand::x2::unpack(orand::x2::mul(r, orand::x2::pack(ca, cb)));
+    z[0] = zz.x;
+    z[1] = orand::x2::unpack(r).x * sa;
+    z[2] = zz.y;
 }
 
 __device__ __forceinline__ void walk3d_x0(const orand::PhiloxKeys &keys, float x[3])
@@ -655,6 +708,7 @@ extern "C" {
 
 orand_status_t orand_brownian_walk(const orand_walk2d_t *p, float *pos_out, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_brownian_walk");
     if (p == nullptr) return ORAND_ERR_INVALID_ARG;
     if (!finite_nonneg(p->dt) || !finite_nonneg(p->D)) return ORAND_ERR_INVALID_ARG;
     if (p->p_first + p->n_particles < p->p_first) return ORAND_ERR_OVERFLOW;
@@ -675,6 +729,7 @@ orand_status_t orand_brownian_walk(const orand_walk2d_t *p, float *pos_out, cuda
 
 orand_status_t orand_walk3d_init(const orand_walk3d_t *p, float *x0, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk3d_init");
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK || a.n == 0) return st;
@@ -688,6 +743,7 @@ orand_status_t orand_walk3d_init(const orand_walk3d_t *p, float *x0, cudaStream_
 orand_status_t orand_walk3d_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *xT,
                                 float *ckpt, double *loss, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk3d_fwd");
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
@@ -719,6 +775,7 @@ orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
                                 const double *grad_loss, double *dmu, double *dsigma, double *dkappa, float *dx0,
                                 cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk3d_bwd");
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
@@ -733,6 +790,7 @@ orand_status_t orand_walk3d_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, const 
 orand_status_t orand_walk3d_plain_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *x,
                                       float *z_store, double *loss, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk3d_plain_fwd");
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
@@ -759,6 +817,7 @@ orand_status_t orand_walk3d_plain_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, 
                                       const float *z_store, const double *grad_loss, double *dmu,
                                       double *dsigma, float *dx0, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk3d_plain_bwd");
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
@@ -793,6 +852,7 @@ orand_status_t orand_walk3d_plain_bwd(orand_ctx_t ctx, const orand_walk3d_t *p, 
 orand_status_t orand_walk3d_stored_fwd(orand_ctx_t ctx, const orand_walk3d_t *p, const float *x0, float *xT,
                                        float *z_store, double *loss, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk3d_stored_fwd");
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
@@ -823,6 +883,7 @@ orand_status_t orand_walk3d_stored_bwd(orand_ctx_t ctx, const orand_walk3d_t *p,
                                        const float *z_store, const double *grad_loss, double *dmu, double *dsigma,
                                        float *dx0, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk3d_stored_bwd");
     Walk3dArgs a;
     orand_status_t st = walk3d_args(p, &a);
     if (st != ORAND_OK) return st;
@@ -847,6 +908,7 @@ orand_status_t orand_walk3d_stored_bwd(orand_ctx_t ctx, const orand_walk3d_t *p,
 
 orand_status_t orand_walk_normals(const uint32_t *words, uint64_t n_pairs, float *out, cudaStream_t stream)
 {
+    ORAND_NVTX_RANGE("orand_walk_normals");
     if (n_pairs == 0) return ORAND_OK;
     if (n_pairs > (UINT64_MAX >> 3)) return ORAND_ERR_OVERFLOW;
     orand_status_t st;

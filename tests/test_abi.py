@@ -192,3 +192,33 @@ def test_stream_statistics_arguments_rejected_on_host(lib):
     assert L.orand_stat_birthday(16, 100, 4, 24, 9, 8, 16, None) == -1            # field past bit 31
     assert L.orand_stat_birthday(16, 100, 4, 24, 8, 0, 16, None) == -1            # r_max = 0
     assert L.orand_stat_birthday(16, 15, 4, 24, 8, 8, 16, None) == 0              # no whole sample
+
+
+def test_injected_allocation_failure_in_ctx_create(lib, monkeypatch):
+    """With ORAND_FAIL_ALLOC=1 every library allocation is refused before the
+    allocator runs; orand_ctx_create reports ORAND_ERR_ALLOC (its host object
+    is allocated before the device is queried) and leaves the handle NULL."""
+    h = ctypes.c_void_p(12345)
+    monkeypatch.setenv("ORAND_FAIL_ALLOC", "1")
+    assert lib.orand_ctx_create(ctypes.byref(h)) == -4
+    assert h.value is None
+    monkeypatch.delenv("ORAND_FAIL_ALLOC")
+    st = lib.orand_ctx_create(ctypes.byref(h))
+    assert st != -4                       # ORAND_OK on a GPU; a device error without one
+    if st == 0:
+        assert lib.orand_ctx_destroy(h) == 0
+
+
+def test_nvtx_ranges_leave_results_unchanged():
+    """ORAND_NVTX=1 wraps each launching call in an NVTX range (for
+    profilers); the calls return what they return without it."""
+    import subprocess
+    import sys
+
+    code = ("import ctypes, paper_2310_19925_b300 as o; L = o._lib(); "
+            "assert L.orand_fill(4, 0, 1, 0, 4, 4, 16, None) == -1; "
+            "assert L.orand_fill_streams(0, 0, 1, 0, 2**64 - 10, 11, 4, 16, None) == -2; "
+            "assert L.orand_engine_draws(0, 0, 0, 0, 0, 5, 0, None) == 0; print('ok')")
+    env = dict(os.environ, ORAND_NVTX="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
