@@ -210,6 +210,64 @@ ORAND_HD uint64_t squares_key(uint64_t key64)
     return h | 1ull;
 }
 
+/* 32-bit addition issued as the integer multiply-add a * one + b, where
+ * `one` is 1 but held in a register whose value the compiler cannot see (a
+ * kernel argument), so it stays a multiply-add and runs on the FMA pipe
+ * rather than the ALU pipe.  Squares' fills use it (their shifts and adds
+ * otherwise load the ALU pipe); the compiler already splits plain adds
+ * between the two pipes where it can, so code that needs no steering keeps
+ * plain adds. */
+struct FmaAdd {
+    uint32_t one;
+    __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const
+    {
+        uint32_t d;
+        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(one), "r"(b));
+        return d;
+    }
+};
+
+/* The Squares word for x = ctr * key (y = x) and z = (ctr + 1) * key, the
+ * same value as squares32(ctr, key), with every step on the FMA pipe: the
+ * cross term 2 xl xh as xl * (xh + xh) with the doubling an FmaAdd, and the
+ * low product's 64-bit sum a wide multiply-add. */
+__device__ __forceinline__ uint64_t sq_add_fma(uint64_t x, uint64_t y, const FmaAdd &add)
+{
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
+    const uint64_t p = (uint64_t)xl * xl + y;
+    uint32_t hi;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(xl), "r"(add(xh, xh)), "r"((uint32_t)(p >> 32)));
+    return ((uint64_t)hi << 32) | (uint32_t)p;
+}
+__device__ __forceinline__ uint32_t squares32_yz(uint64_t y, uint64_t z, const FmaAdd &add)
+{
+    uint64_t x = swap_halves(sq_add_fma(y, y, add));
+    x = swap_halves(sq_add_fma(x, z, add));
+    x = swap_halves(sq_add_fma(x, y, add));
+    return (uint32_t)(sq_add_fma(x, z, add) >> 32);
+}
+/* y + key modulo 2^64 on the FMA pipe: a wide multiply-add of the key's low
+ * word by one, then the high words. */
+__device__ __forceinline__ uint64_t add64_fma(uint64_t y, uint64_t key, const FmaAdd &add)
+{
+    uint64_t r;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"((uint32_t)key), "r"(add.one), "l"(y));
+    return ((uint64_t)add((uint32_t)(r >> 32), (uint32_t)(key >> 32)) << 32) | (uint32_t)r;
+}
+/* Words 4b..4b+3: consecutive counters ctr, ctr + 1, ... share their products,
+ * (ctr + 1) key = ctr key + key, so one 64-bit multiply and four additions
+ * give every x and z. */
+__device__ __forceinline__ uint4 squares_block_fma(uint64_t sq_key, uint32_t counter, uint32_t b_idx,
+                                                   const FmaAdd &add)
+{
+    const uint64_t base = ((uint64_t)counter << 32) | ((uint64_t)b_idx << 2);
+    const uint64_t y0 = base * sq_key;
+    const uint64_t y1 = add64_fma(y0, sq_key, add), y2 = add64_fma(y1, sq_key, add);
+    const uint64_t y3 = add64_fma(y2, sq_key, add), y4 = add64_fma(y3, sq_key, add);
+    return make_uint4(squares32_yz(y0, y1, add), squares32_yz(y1, y2, add), squares32_yz(y2, y3, add),
+                      squares32_yz(y3, y4, add));
+}
+
 /* Four consecutive Squares words 4b..4b+3 of stream (key, counter). */
 ORAND_HD uint4 squares_block(uint64_t sq_key, uint32_t counter, uint32_t b_idx)
 {
