@@ -45,8 +45,15 @@ METRIC = "Philox u32 fill GB/s vs HBM peak; walk particle-steps/s; adjoint vs pl
 # Issue peak of the integer/FP32 pipes: 148 SMs x 4 schedulers x 32 lanes x
 # 2.032 GHz (the B300's unit counts and maximum SM clock), in lane-operations/s.
 ALU_PEAK = 148 * 128 * 2.032e9
-# Operations per 2D particle-step: the lane-instructions the kernel's source
-# needs per step, confirmed by ncu (at 2^20 x 1000): Philox4x32-10 with
+# Algorithmic work per particle-step, in scalar lane-operations: what one
+# step needs when every operation is a scalar instruction (the count ncu
+# measured for the scalar form of each kernel).  The kernels now issue the
+# FP32 part of the walks' map as packed pairs (one f32x2 instruction does two
+# of these operations), so they issue fewer instructions than this count;
+# `frac` is the work rate against the issue peak, and `issue_frac` (from the
+# committed ncu count of the current kernels) the share of issue slots used.
+# 2D, per particle-step: the lane-instructions the scalar kernel needed
+# per step, confirmed by ncu (at 2^20 x 1000): Philox4x32-10 with
 # the two used words and the constant counter words folded (33), the walks'
 # Box-Muller radius (u1 and v, the six-term series with its factor 2 folded
 # in, the log2 and square-root estimates, the selection) and angle (the 22
@@ -104,6 +111,19 @@ def source_hash(paths):
 
 # Issue peak in warp-instructions/s: 148 SMs x 4 schedulers x 2.032 GHz.
 ISSUE_PEAK_WARP_INST = 148 * 4 * 2.032e9
+
+
+def walk_issue_counts():
+    """kernel key -> (source hash, lane-instructions per particle-step) from
+    the committed ncu summary of the walk kernels."""
+    p = os.path.join(ROOT, "profiles", "walk_issue.txt")
+    out = {}
+    if os.path.exists(p):
+        for line in open(p):
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#"):
+                out[parts[0]] = (parts[1], float(parts[2]))
+    return out
 
 
 def fill_issue_counts(src_hash):
@@ -778,22 +798,28 @@ def main():
     # (the 2D walk, and the 3D walks' forward + adjoint pairs; issue-bound)
     # against the issue peak.
     rooflines = {}
-    w2 = row_table.get("walk2d/fused")
-    if w2:
-        ops = w2["particle-steps_per_s"] / world * WALK2D_OPS_PER_STEP
-        rooflines["walk2d_kernel"] = {"bound": "alu", "achieved": ops, "peak": ALU_PEAK, "unit": "lane-ops/s",
-                                      "frac": ops / ALU_PEAK, "ops_per_particle_step": WALK2D_OPS_PER_STEP,
-                                      "share_of_step": w2["share_of_step"],
-                                      "peak_kind": "derived: 148 SMs x 128 lanes x 2.032 GHz"}
-    for row, key, opc in [("walk3d/fused_fwd+adjoint", "walk3d_fwd_kernel<0>+walk3d_bwd_kernel<0>", WALK3D_OPS_PER_STEP),
+    walk_src = source_hash(DOMINANT_KERNEL_SOURCES)
+    walk_issue = walk_issue_counts()
+
+    def issued(key, rate):
+        h, per_step = walk_issue.get(key, (None, None))
+        if h != walk_src or per_step is None:
+            return None, None
+        return per_step, per_step * rate / ALU_PEAK
+
+    for row, key, opc in [("walk2d/fused", "walk2d_kernel", WALK2D_OPS_PER_STEP),
+                          ("walk3d/fused_fwd+adjoint", "walk3d_fwd_kernel<0>+walk3d_bwd_kernel<0>", WALK3D_OPS_PER_STEP),
                           ("walk3d/ou_fused_fwd+adjoint", "walk3d_fwd_kernel<1>+walk3d_bwd_kernel<1>",
                            WALK3D_OU_OPS_PER_STEP)]:
-        w3 = row_table.get(row)
-        if w3:
-            ops = w3["particle-steps_per_s"] / world * opc
+        w = row_table.get(row)
+        if w:
+            rate = w["particle-steps_per_s"] / world
+            ops = rate * opc
+            per_step, ifrac = issued(key, rate)
             rooflines[key] = {"bound": "alu", "achieved": ops, "peak": ALU_PEAK, "unit": "lane-ops/s",
                               "frac": ops / ALU_PEAK, "ops_per_particle_step": opc,
-                              "share_of_step": w3["share_of_step"],
+                              "issued_lane_instructions_per_particle_step": per_step, "issue_frac": ifrac,
+                              "share_of_step": w["share_of_step"],
                               "peak_kind": "derived: 148 SMs x 128 lanes x 2.032 GHz"}
     # The headline metric's kernel: the Philox u32 fill against the measured
     # copy bandwidth, with its ncu DRAM traffic.

@@ -455,12 +455,13 @@ __device__ __forceinline__ float bm_radius(uint32_t w0)
     /* sqrt(x) without the special-case branch of the IEEE square root:
      * y ~ 1/sqrt(x) from the hardware estimate, s = x y, then one Newton step
      * on the exact residual x - s^2 (an FMA).  x is +0 or a normal number in
-     * [2^-23, 34], so no special case can occur; x = 0 gives 0 by the select. */
-    const float y = rsqrtf(x);
+     * [2^-23, 34], so no special case can occur.  The estimate takes
+     * max(x, 2^-100): the same as x for every x > 0, and finite at x = 0,
+     * where s = 0, the residual +0 and the step give r = +0 exactly. */
+    const float y = rsqrtf(fmaxf(x, 0x1p-100f));
     const float sx = x * y;
     const float res = fmaf(-sx, sx, x);
-    const float r = fmaf(0.5f * y, res, sx);
-    return x > 0.0f ? r : 0.0f;
+    return fmaf(0.5f * y, res, sx);
 }
 
 /* (cos, sin)(2 pi u2), u2 = (w1 >> 8) * 2^-24: quadrant q = round(4 u2),
@@ -582,10 +583,10 @@ __device__ __forceinline__ uint4 box_muller2_f32(uint4 w)
     const unsigned long long x = fma(splat(-2.0f), lnu, splat(0.0f));      /* -2 ln u1 >= +0 */
     const unsigned long long nx = mul(splat(2.0f), lnu);                    /* -x where x > 0 */
     const float2 xs = unpack(x);
-    const unsigned long long y = pack(rsqrtf(xs.x), rsqrtf(xs.y));
+    const unsigned long long y = pack(rsqrtf(fmaxf(xs.x, 0x1p-100f)), rsqrtf(fmaxf(xs.y, 0x1p-100f)));
     const unsigned long long sx = mul(x, y);
     const float2 rr = unpack(fma(mul(splat(-0.5f), y), fma(sx, sx, nx), sx));
-    const float ra = xs.x > 0.0f ? rr.x : 0.0f, rb = xs.y > 0.0f ? rr.y : 0.0f;
+    const float ra = rr.x, rb = rr.y;
     const unsigned long long r = fma(pack(__uint2float_rn((w.y + (1u << 29)) & 0x3FFFFF00u),
                                           __uint2float_rn((w.w + (1u << 29)) & 0x3FFFFF00u)),
                                      splat(0x1p-31f), splat(-0.25f));
