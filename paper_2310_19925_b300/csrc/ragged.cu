@@ -696,7 +696,8 @@ static bool env_flag(const char *name, bool dflt)
 // $HOME/.cache/orand/ragged_tune.txt.  It is read once per process and
 // appended to after each new tuning; unreadable or malformed lines are
 // skipped, so a bad file costs a re-tune, never a wrong result (every
-// configuration writes the same bits).
+// configuration writes the same bits).  With no file every context tunes
+// its own size classes.
 using TuneKey = std::tuple<std::string, int, int, int>;
 
 struct TuneFile {
@@ -771,6 +772,7 @@ static bool tune_file_lookup(const TuneKey &k, RaggedConfig *cfg)
     TuneFile &f = tune_file();
     std::lock_guard<std::mutex> lock(f.mu);
     tune_file_load(f);
+    if (f.path.empty()) return false;  // no file: each context tunes for itself
     auto it = f.table.find(k);
     if (it == f.table.end()) return false;
     *cfg = it->second;
@@ -782,8 +784,8 @@ static void tune_file_store(const TuneKey &k, const RaggedConfig &c)
     TuneFile &f = tune_file();
     std::lock_guard<std::mutex> lock(f.mu);
     tune_file_load(f);
-    f.table[k] = c;
     if (f.path.empty()) return;
+    f.table[k] = c;
     // Create the parent directories if needed (best effort; existing ones stay).
     for (size_t i = f.path.find('/', 1); i != std::string::npos; i = f.path.find('/', i + 1))
         mkdir(f.path.substr(0, i).c_str(), 0755);
