@@ -61,7 +61,11 @@ ALU_PEAK = 148 * 128 * 2.032e9
 # multiply the compiler puts before them, swap and signs from w1's top bits)
 # about 30 together, two FMA sums (2; the block sum is scaled by s once),
 # and the Kahan add of each 16-step block sum and the unrolled loop's
-# control (2).
+# control (2).  This count is kept as the fixed unit of work per step: the
+# angle now takes a half-turn split (the sign on the radius, no swap), which
+# needs about five operations fewer, so `frac` counts the same work per step
+# as before and rises with throughput, while `issue_frac` counts what the
+# current kernel issues.
 WALK2D_OPS_PER_STEP = 67
 # The same per 3D particle-step, forward plus adjoint (ncu-confirmed;
 # with the OU drift 112.6 + 123.3 by ncu): Philox with all four words, two radii, a

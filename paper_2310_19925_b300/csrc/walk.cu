@@ -102,7 +102,10 @@ constexpr uint32_t kSumBlock = 16;
 // pairs at once, (radius word, angle word) = (u_a, t_a) in lane 0 and
 // (u_b, t_b) in lane 1, with its FP32 arithmetic on packed pairs (each lane
 // rounded as the scalar map, so the same bits): the radii as a packed pair,
-// and each angle's quadrant-adjusted cosine and sine.
+// each carrying its angle's half-turn sign, and each angle's cosine and sine
+// at phi in [0, pi).  radius * cosine and radius * sine are then the
+// products of bm_radius_walk and bm_cos_sin_walk bit for bit (a sign flip is
+// exact).
 __device__ __forceinline__ unsigned long long walk_map_x2(uint32_t u_a, uint32_t t_a, uint32_t u_b, uint32_t t_b,
                                                           float &ca, float &sa, float &cb, float &sb)
 {
@@ -120,11 +123,16 @@ __device__ __forceinline__ unsigned long long walk_map_x2(uint32_t u_a, uint32_t
     const float2 x_log = unpack(mul(splat(-1.3862943611198906f), pack(orand::sfu_lg2(uu.x), orand::sfu_lg2(uu.y))));
     const float2 vv = unpack(v);
     const float xa = vv.x < 0.0625f ? x_series.x : x_log.x, xb = vv.y < 0.0625f ? x_series.y : x_log.y;
-    const float2 th = unpack(mul(pack((float)(t_a & 0x3FFFFF00u), (float)(t_b & 0x3FFFFF00u)),
+    const float2 ph = unpack(mul(pack((float)(t_a & 0x7FFFFF00u), (float)(t_b & 0x7FFFFF00u)),
                                  splat(0x1p-31f * 3.14159265358979324f)));
-    orand::bm_quadrant_walk(t_a, orand::sfu_sin(th.x), orand::sfu_cos(th.x), &ca, &sa);
-    orand::bm_quadrant_walk(t_b, orand::sfu_sin(th.y), orand::sfu_cos(th.y), &cb, &sb);
-    return pack(orand::sfu_sqrt(xa), orand::sfu_sqrt(xb));
+    ca = orand::sfu_cos(ph.x);
+    sa = orand::sfu_sin(ph.x);
+    cb = orand::sfu_cos(ph.y);
+    sb = orand::sfu_sin(ph.y);
+    // The half-turn sign (bit 31 of the angle word) on the radius: the same
+    // products as bm_cos_sin_walk's signed cosine and sine, one xor per pair.
+    return pack(__uint_as_float(__float_as_uint(orand::sfu_sqrt(xa)) ^ (t_a & 0x80000000u)),
+                __uint_as_float(__float_as_uint(orand::sfu_sqrt(xb)) ^ (t_b & 0x80000000u)));
 }
 
 // Steps t (lane 0) and t + 1 (lane 1) of a 2D walk from their Philox blocks
