@@ -159,8 +159,9 @@ orand_status_t orand_ctx_destroy(orand_ctx_t ctx);
  * with counter (0, 0, 0, 0).  Step t = 1..steps adds s * (z0, z1), where
  * (z0, z1) is Box-Muller of words 0 and 1 of the block with counter
  * (0, t, 0, 0) and s = sqrt(2 D dt) (rounded once to FP32).  The sum is
- * compensated per block of 16 steps: the block's increments are summed with
- * FMAs and each block sum is added to the position with Kahan compensation.
+ * compensated per block of 32 steps: the block's increments are summed with
+ * FMAs (odd and even steps apart) and each block sum is added to the
+ * position with Kahan compensation.
  * pos_out: 2 * n_particles floats (x, y interleaved), 8-byte aligned.
  * Errors: INVALID_ARG (NULL p or pos_out with n > 0, dt or D negative or
  * not finite), OVERFLOW (p_first + n wraps, steps = 2^32 - 1), ALIGNMENT,

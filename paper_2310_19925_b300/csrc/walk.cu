@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 // The 2D kernel is bound by instruction issue (67 scalar operations per
 // particle-step, nearly all of them the Philox rounds and Box-Muller).  One
 // particle per thread; the position sum is compensated per block of
-// kSumBlock steps (plain FMA sums inside a block, a Kahan add of each block
+// kSumBlock2d steps (plain FMA sums inside a block, a Kahan add of each block
 // sum), which saves the per-step compensation while keeping the rounding
 // error of the whole walk at the level of one FP32 rounding per block sum.
 // A full block takes its steps in pairs: the two steps' Philox blocks are
@@ -88,15 +88,45 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 // run as packed pairs (one f32x2 instruction for both steps; each lane is
 // rounded as the scalar operation, so every normal has the same bits; only
 // the block sum is split into an even-step and an odd-step half).  The loop
-// over the 8 pairs is unrolled by 2, and with the launch bound of one block
-// per SM ptxas keeps the round keys in registers (66 registers).  Measured on
-// B300 (full walk, 2^24 x 10^4): 425.5 ms against 433.8 with scalar steps
-// unrolled by 4; pairs unrolled by 1 or 4 took 436.3 and 427.3 ms.  Earlier,
+// over the 16 pairs is unrolled by 2, and with the launch bound of one block
+// per SM ptxas keeps the round keys in registers (72 registers).  Measured on
+// B300 (full walk, 2^24 x 10^4, 16-step blocks): 425.5 ms against 433.8 with
+// scalar steps unrolled by 4; pairs unrolled by 1 or 4 took 436.3 and 427.3
+// ms.  Earlier,
 // with scalar steps: two particles per thread 437.9 ms, three or four
 // slower still, and launch bounds that fit 32 or 40 warps per SM
-// 436.6-446.1 ms.
+// 436.6-446.1 ms.  With the half-turn angle split: 404.3 ms; the map's
+// packed constants read from constant memory (below) 400.1 ms; and block
+// sums of 32 steps instead of 16 (half the Kahan adds and loop control per
+// step; each half of a block sum then adds 16 terms instead of 8) 396.3 ms.
 constexpr int kWalk2dBlock = 256;
-constexpr uint32_t kSumBlock = 16;
+constexpr uint32_t kSumBlock = 16;      // the 3D walks
+constexpr uint32_t kSumBlock2d = 32;    // the 2D walk
+
+// The walks' map's FP32 constants as packed pairs (both lanes the same).
+// The 2D kernel reads them from constant memory once, before its step loop;
+// written as immediates, ptxas re-creates some of them inside the loop
+// (ncu, 2^20 x 1000: 60.2 against 59.1 instructions per particle-step).
+// The 3D kernels measured slower that way (117.1 against 116.6 ms) and keep
+// the immediates.
+struct WalkMapConsts {
+    unsigned long long u1_scale, minus_one, one, c3, c4, c5, c6, two, log_scale, angle_scale;
+};
+__device__ __forceinline__ WalkMapConsts walk_map_consts_imm()
+{
+    using namespace orand::x2;
+    return {splat(0x1p-24f), splat(-1.0f), splat(1.0f), splat(2.0f / 6.0f), splat(0.4f), splat(0.5f),
+            splat(2.0f / 3.0f), splat(2.0f), splat(-1.3862943611198906f), splat(0x1p-31f * 3.14159265358979324f)};
+}
+static __constant__ float2 kWalkMapConsts[10] = {
+    {0x1p-24f, 0x1p-24f}, {-1.0f, -1.0f}, {1.0f, 1.0f}, {2.0f / 6.0f, 2.0f / 6.0f}, {0.4f, 0.4f}, {0.5f, 0.5f},
+    {2.0f / 3.0f, 2.0f / 3.0f}, {2.0f, 2.0f}, {-1.3862943611198906f, -1.3862943611198906f},
+    {0x1p-31f * 3.14159265358979324f, 0x1p-31f * 3.14159265358979324f}};
+__device__ __forceinline__ WalkMapConsts walk_map_consts_loaded()
+{
+    const unsigned long long *p = reinterpret_cast<const unsigned long long *>(kWalkMapConsts);
+    return {p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9]};
+}
 
 // The walks' Box-Muller map (bm_radius_walk, bm_cos_sin_walk) for two
 // pairs at once, (radius word, angle word) = (u_a, t_a) in lane 0 and
@@ -107,24 +137,24 @@ constexpr uint32_t kSumBlock = 16;
 // products of bm_radius_walk and bm_cos_sin_walk bit for bit (a sign flip is
 // exact).
 __device__ __forceinline__ unsigned long long walk_map_x2(uint32_t u_a, uint32_t t_a, uint32_t u_b, uint32_t t_b,
-                                                          float &ca, float &sa, float &cb, float &sb)
+                                                          float &ca, float &sa, float &cb, float &sb,
+                                                          const WalkMapConsts &k = walk_map_consts_imm())
 {
     using namespace orand::x2;
     const unsigned long long u1 = mul(pack(__uint2float_rn((u_a >> 8) + 1u), __uint2float_rn((u_b >> 8) + 1u)),
-                                      splat(0x1p-24f));
-    const unsigned long long v = fma(u1, splat(-1.0f), splat(1.0f));              /* 1 - u1 */
-    unsigned long long p2 = fma(v, splat(2.0f / 6.0f), splat(0.4f));
-    p2 = fma(p2, v, splat(0.5f));
-    p2 = fma(p2, v, splat(2.0f / 3.0f));
-    p2 = fma(p2, v, splat(1.0f));
-    p2 = fma(p2, v, splat(2.0f));
+                                      k.u1_scale);
+    const unsigned long long v = fma(u1, k.minus_one, k.one);                   /* 1 - u1 */
+    unsigned long long p2 = fma(v, k.c3, k.c4);
+    p2 = fma(p2, v, k.c5);
+    p2 = fma(p2, v, k.c6);
+    p2 = fma(p2, v, k.one);
+    p2 = fma(p2, v, k.two);
     const float2 x_series = unpack(mul(v, p2));
     const float2 uu = unpack(u1);
-    const float2 x_log = unpack(mul(splat(-1.3862943611198906f), pack(orand::sfu_lg2(uu.x), orand::sfu_lg2(uu.y))));
+    const float2 x_log = unpack(mul(k.log_scale, pack(orand::sfu_lg2(uu.x), orand::sfu_lg2(uu.y))));
     const float2 vv = unpack(v);
     const float xa = vv.x < 0.0625f ? x_series.x : x_log.x, xb = vv.y < 0.0625f ? x_series.y : x_log.y;
-    const float2 ph = unpack(mul(pack((float)(t_a & 0x7FFFFF00u), (float)(t_b & 0x7FFFFF00u)),
-                                 splat(0x1p-31f * 3.14159265358979324f)));
+    const float2 ph = unpack(mul(pack((float)(t_a & 0x7FFFFF00u), (float)(t_b & 0x7FFFFF00u)), k.angle_scale));
     ca = orand::sfu_cos(ph.x);
     sa = orand::sfu_sin(ph.x);
     cb = orand::sfu_cos(ph.y);
@@ -138,11 +168,11 @@ __device__ __forceinline__ unsigned long long walk_map_x2(uint32_t u_a, uint32_t
 // Steps t (lane 0) and t + 1 (lane 1) of a 2D walk from their Philox blocks
 // wa, wb, accumulated into the packed block sums.
 __device__ __forceinline__ void walk2d_step_pair(uint4 wa, uint4 wb, unsigned long long &sxx,
-                                                 unsigned long long &syy)
+                                                 unsigned long long &syy, const WalkMapConsts &k)
 {
     using namespace orand::x2;
     float ca, sa, cb, sb;
-    const unsigned long long r = walk_map_x2(wa.x, wa.y, wb.x, wb.y, ca, sa, cb, sb);
+    const unsigned long long r = walk_map_x2(wa.x, wa.y, wb.x, wb.y, ca, sa, cb, sb, k);
     sxx = fma(r, pack(ca, cb), sxx);
     syy = fma(r, pack(sa, sb), syy);
 }
@@ -153,18 +183,19 @@ __global__ void __launch_bounds__(kWalk2dBlock, 1) walk2d_kernel(uint64_t n, uin
     const uint64_t i = (uint64_t)blockIdx.x * kWalk2dBlock + threadIdx.x;
     if (i >= n) return;
     const orand::PhiloxKeys keys(seed ^ (p_first + i));
+    const WalkMapConsts mk = walk_map_consts_loaded();
     const uint4 w0 = keys.block(0u, 0u);
     float x = orand::u01_f32(w0.x), y = orand::u01_f32(w0.y), cx = 0.f, cy = 0.f;
-    // t runs 1..steps in blocks of kSumBlock; `done` counts steps taken so
+    // t runs 1..steps in blocks of kSumBlock2d; `done` counts steps taken so
     // the loop cannot wrap when steps is near 2^32.
     for (uint32_t done = 0; done < steps;) {
-        const uint32_t len = min(kSumBlock, steps - done);
+        const uint32_t len = min(kSumBlock2d, steps - done);
         float sx = 0.f, sy = 0.f;
-        if (len == kSumBlock) {
+        if (len == kSumBlock2d) {
             unsigned long long sxx = orand::x2::splat(0.0f), syy = orand::x2::splat(0.0f);
 #pragma unroll 2
-            for (uint32_t k = 1; k <= kSumBlock; k += 2)
-                walk2d_step_pair(keys.block(0u, done + k), keys.block(0u, done + k + 1), sxx, syy);
+            for (uint32_t k = 1; k <= kSumBlock2d; k += 2)
+                walk2d_step_pair(keys.block(0u, done + k), keys.block(0u, done + k + 1), sxx, syy, mk);
             const float2 a = orand::x2::unpack(sxx), b = orand::x2::unpack(syy);
             sx = a.x + a.y;
             sy = b.x + b.y;
