@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 // The 2D kernel is bound by instruction issue (67 scalar operations per
 // particle-step, nearly all of them the Philox rounds and Box-Muller).  One
 // particle per thread; the position sum is compensated per block of
-// kSumBlock2d steps (plain FMA sums inside a block, a Kahan add of each block
+// kSumBlock steps (plain FMA sums inside a block, a Kahan add of each block
 // sum), which saves the per-step compensation while keeping the rounding
 // error of the whole walk at the level of one FP32 rounding per block sum.
 // A full block takes its steps in pairs: the two steps' Philox blocks are
@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 // sums of 32 steps instead of 16 (half the Kahan adds and loop control per
 // step; each half of a block sum then adds 16 terms instead of 8) 396.3 ms.
 constexpr int kWalk2dBlock = 256;
-constexpr uint32_t kSumBlock = 16;      // the 3D walks
-constexpr uint32_t kSumBlock2d = 32;    // the 2D walk
+// Steps per block sum, every walk.  3D (2^22 x 4096, forward + adjoint):
+// 116.5 ms with 16-step blocks, 115.4 with 32 (OU 133.2 and 132.6).
+constexpr uint32_t kSumBlock = 32;
 
 // The walks' map's FP32 constants as packed pairs (both lanes the same).
 // The 2D kernel reads them from constant memory once, before its step loop;
@@ -186,15 +187,15 @@ __global__ void __launch_bounds__(kWalk2dBlock, 1) walk2d_kernel(uint64_t n, uin
     const WalkMapConsts mk = walk_map_consts_loaded();
     const uint4 w0 = keys.block(0u, 0u);
     float x = orand::u01_f32(w0.x), y = orand::u01_f32(w0.y), cx = 0.f, cy = 0.f;
-    // t runs 1..steps in blocks of kSumBlock2d; `done` counts steps taken so
+    // t runs 1..steps in blocks of kSumBlock; `done` counts steps taken so
     // the loop cannot wrap when steps is near 2^32.
     for (uint32_t done = 0; done < steps;) {
-        const uint32_t len = min(kSumBlock2d, steps - done);
+        const uint32_t len = min(kSumBlock, steps - done);
         float sx = 0.f, sy = 0.f;
-        if (len == kSumBlock2d) {
+        if (len == kSumBlock) {
             unsigned long long sxx = orand::x2::splat(0.0f), syy = orand::x2::splat(0.0f);
 #pragma unroll 2
-            for (uint32_t k = 1; k <= kSumBlock2d; k += 2)
+            for (uint32_t k = 1; k <= kSumBlock; k += 2)
                 walk2d_step_pair(keys.block(0u, done + k), keys.block(0u, done + k + 1), sxx, syy, mk);
             const float2 a = orand::x2::unpack(sxx), b = orand::x2::unpack(syy);
             sx = a.x + a.y;
