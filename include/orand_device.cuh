@@ -402,6 +402,13 @@ __device__ __forceinline__ double u01_f64_nb(uint32_t hi, uint32_t lo)
     return __hiloint2double(zero ? 0 : (int)rh, zero ? 0 : (int)tl);
 }
 
+/* The SFU's estimates as PTX instructions (lg2.approx, sin.approx, cos.approx,
+ * sqrt.approx), used by both Box-Muller maps below. */
+__device__ __forceinline__ float sfu_lg2(float x) { float y; asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_sin(float x) { float y; asm("sin.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_cos(float x) { float y; asm("cos.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sfu_sqrt(float x) { float y; asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+
 /* ---------------------------------------------------------- Box-Muller */
 /*
  * r = sqrt(-2 ln u1) and (cos, sin)(2 pi u2), specialised to this library's
@@ -409,9 +416,10 @@ __device__ __forceinline__ double u01_f64_nb(uint32_t hi, uint32_t lo)
  * integer m in [0, 2^24).  Method: argument reduction plus polynomials
  * (Cody & Waite 1980; Muller, "Elementary Functions", 2016).  The
  * coefficients are this library's own near-minimax fits
- * (paper_2310_19925_b300/csrc/fit_boxmuller.py).  Measured on every input
- * against FP64: r within 0.97 ulp, sin and cos within 1.02 ulp, exact zeros
- * exact.  Each normal is within 3 ulp of the correctly rounded FP64 value.
+ * (paper_2310_19925_b300/csrc/fit_boxmuller.py); the square root is the SFU's
+ * estimate.  Measured on every input against FP64: r within 1 ulp, sin and
+ * cos within 1.02 ulp, exact zeros exact.  Each normal is within 3 ulp of the
+ * correctly rounded FP64 value (2^24 random pairs).
  */
 namespace bm {
 constexpr float LN2_HI = 0x1.62e400p-1f;     /* ln 2, 16 significant bits: E * LN2_HI is exact */
@@ -452,16 +460,11 @@ __device__ __forceinline__ float bm_radius(uint32_t w0)
     const float lnf = fmaf(g * g, p, g);
     const float lnu = fmaf(E, bm::LN2_HI, fmaf(E, bm::LN2_LO, lnf));
     const float x = fmaf(-2.0f, lnu, 0.0f);                    /* -2 ln u1 >= +0 */
-    /* sqrt(x) without the special-case branch of the IEEE square root:
-     * y ~ 1/sqrt(x) from the hardware estimate, s = x y, then one Newton step
-     * on the exact residual x - s^2 (an FMA).  x is +0 or a normal number in
-     * [2^-23, 34], so no special case can occur.  The estimate takes
-     * max(x, 2^-100): the same as x for every x > 0, and finite at x = 0,
-     * where s = 0, the residual +0 and the step give r = +0 exactly. */
-    const float y = rsqrtf(fmaxf(x, 0x1p-100f));
-    const float sx = x * y;
-    const float res = fmaf(-sx, sx, x);
-    return fmaf(0.5f * y, res, sx);
+    /* x is +0 or a normal number in [2^-23, 34].  The SFU's square-root
+     * estimate keeps r within 1 ulp over all 2^24 inputs (against 0.97 ulp
+     * for a reciprocal-square-root estimate plus one Newton step, in five
+     * instructions more) and gives +0 at x = +0. */
+    return sfu_sqrt(x);
 }
 
 /* (cos, sin)(2 pi u2), u2 = (w1 >> 8) * 2^-24: quadrant q = round(4 u2),
@@ -557,9 +560,7 @@ __device__ __forceinline__ unsigned long long add(unsigned long long a, unsigned
  * as (z0, z1, z2, z3) bit patterns: the operations of bm_radius and
  * bm_cos_sin done on packed pairs (lane 0 the first pair, lane 1 the
  * second), so the same bits as two box_muller_f32 calls in about two thirds
- * of the instructions.  The radius's tail is rearranged without changing a
- * rounding: 2 ln u1 is -x exactly, so x - (x y)^2 is the negation of
- * fma(x y, x y, 2 ln u1), folded into -0.5 y. */
+ * of the instructions. */
 __device__ __forceinline__ uint4 box_muller2_f32(uint4 w)
 {
     using namespace x2;
@@ -580,13 +581,8 @@ __device__ __forceinline__ uint4 box_muller2_f32(uint4 w)
     p = fma(p, g, splat(bm::PL0));
     const unsigned long long lnf = fma(mul(g, g), p, g);
     const unsigned long long lnu = fma(E, splat(bm::LN2_HI), fma(E, splat(bm::LN2_LO), lnf));
-    const unsigned long long x = fma(splat(-2.0f), lnu, splat(0.0f));      /* -2 ln u1 >= +0 */
-    const unsigned long long nx = mul(splat(2.0f), lnu);                    /* -x where x > 0 */
-    const float2 xs = unpack(x);
-    const unsigned long long y = pack(rsqrtf(fmaxf(xs.x, 0x1p-100f)), rsqrtf(fmaxf(xs.y, 0x1p-100f)));
-    const unsigned long long sx = mul(x, y);
-    const float2 rr = unpack(fma(mul(splat(-0.5f), y), fma(sx, sx, nx), sx));
-    const float ra = rr.x, rb = rr.y;
+    const float2 xs = unpack(fma(splat(-2.0f), lnu, splat(0.0f)));        /* -2 ln u1 >= +0 */
+    const float ra = sfu_sqrt(xs.x), rb = sfu_sqrt(xs.y);
     const unsigned long long r = fma(pack(__uint2float_rn((w.y + (1u << 29)) & 0x3FFFFF00u),
                                           __uint2float_rn((w.w + (1u << 29)) & 0x3FFFFF00u)),
                                      splat(0x1p-31f), splat(-0.25f));
@@ -626,10 +622,6 @@ __device__ __forceinline__ float box_muller_cos_f32(uint32_t w0, uint32_t w1)
  * cosine and sine within 3.4e-7 absolute of cos and sin(2 pi u2).  The fills
  * keep the map above (within 3 ulp). */
 
-__device__ __forceinline__ float sfu_lg2(float x) { float y; asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float sfu_sin(float x) { float y; asm("sin.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float sfu_cos(float x) { float y; asm("cos.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
-__device__ __forceinline__ float sfu_sqrt(float x) { float y; asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
 
 /* sqrt(-2 ln u1), u1 = ((w0 >> 8) + 1) 2^-24.  With v = 1 - u1 (exact):
  * for v < 1/16, -2 ln(1 - v) = 2 v (1 + v/2 + v^2/3 + v^3/4 + v^4/5 + v^5/6)
