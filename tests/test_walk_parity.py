@@ -44,7 +44,7 @@ def pos_close(gpu, ref, scale=1.0):
 
 # ------------------------------------------------------------------- 2D ----
 
-@pytest.mark.parametrize("steps", [0, 1, 37, 1000])
+@pytest.mark.parametrize("steps", [0, 1, 31, 32, 37, 64, 1000])
 @pytest.mark.parametrize("p_first", [0, 2**40 + 5])
 def test_walk2d_small(torch_cuda, orc, steps, p_first):
     n = 1000
