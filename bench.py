@@ -822,6 +822,9 @@ def main():
             per_step, ifrac = issued(key, rate)
             rooflines[key] = {"bound": "alu", "achieved": ops, "peak": ALU_PEAK, "unit": "lane-ops/s",
                               "frac": ops / ALU_PEAK, "ops_per_particle_step": opc,
+                              "ops_kind": "fixed unit of work per particle-step (the scalar kernel's instruction "
+                                          "count for one Philox block, the Box-Muller map and the sums); "
+                                          "issue_frac counts the instructions the current kernel issues",
                               "issued_lane_instructions_per_particle_step": per_step, "issue_frac": ifrac,
                               "share_of_step": w["share_of_step"],
                               "peak_kind": "derived: 148 SMs x 128 lanes x 2.032 GHz"}
