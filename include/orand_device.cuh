@@ -29,9 +29,10 @@
  * one FP32 conversion (no FP64 arithmetic);
  * Box-Muller with u1 = ((w0>>8)+1) * 2^-24, u2 = (w1>>8) * 2^-24,
  * r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2), using the library's own
- * reduced-range log and sincospi (within 3 ulp of the FP64 values).  The
- * walk kernels use a cheaper map of the same form (bm_radius_walk,
- * bm_cos_sin_walk), accurate to about 1e-6.
+ * reduced-range log and sincospi and the SFU's square root (within 3 ulp of
+ * the FP64 values).  The walk kernels use a cheaper map of the same form
+ * (bm_radius_walk, bm_cos_sin_walk: SFU log2, sin and cos, a half-turn
+ * split of the angle), accurate to about 1e-6.
  */
 #pragma once
 

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 
 // ------------------------------------------------------------------ 2D walk
 
-// The 2D kernel is bound by instruction issue (67 scalar operations per
+// The 2D kernel is bound by instruction issue (58 instructions per
 // particle-step, nearly all of them the Philox rounds and Box-Muller).  One
 // particle per thread; the position sum is compensated per block of
 // kSumBlock steps (plain FMA sums inside a block, a Kahan add of each block
@@ -92,9 +92,8 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *__re
 // per SM ptxas keeps the round keys in registers (72 registers).  Measured on
 // B300 (full walk, 2^24 x 10^4, 16-step blocks): 425.5 ms against 433.8 with
 // scalar steps unrolled by 4; pairs unrolled by 1 or 4 took 436.3 and 427.3
-// ms.  Earlier,
-// with scalar steps: two particles per thread 437.9 ms, three or four
-// slower still, and launch bounds that fit 32 or 40 warps per SM
+// ms.  Earlier, with scalar steps: two particles per thread 437.9 ms, three
+// or four slower still, and launch bounds that fit 32 or 40 warps per SM
 // 436.6-446.1 ms.  With the half-turn angle split: 404.3 ms; the map's
 // packed constants read from constant memory (below) 400.1 ms; and block
 // sums of 32 steps instead of 16 (half the Kahan adds and loop control per
